@@ -1,0 +1,136 @@
+/*
+ * gpk.h -- C ABI of libgpk: low-precision matrix-free Gaussian-process solves
+ * on one NVIDIA GB300 (sm_103a).
+ *
+ * The library implements the hot path of "Low-Precision Arithmetic for Fast
+ * Gaussian Processes" (Maddox, Potapczynski & Wilson, 2022): the matrix-free
+ * kernel MVM of Eq. mvm on tensor cores in FP16/BF16 with FP32 accumulation,
+ * inside the enhanced-stability preconditioned conjugate-gradient solve of
+ * Alg. 2 (log-scale step sizes, re-orthogonalisation, pivoted-Cholesky /
+ * Woodbury preconditioner of Eq. woodbury), and the pseudo-loss gradient of
+ * Eq. approx.
+ *
+ * Conventions shared by every entry point
+ *   - Return GP_OK (0) or a negative GP_ERR_* status; nothing is thrown.
+ *   - Pointers named "device" are CUDA device pointers owned by the caller;
+ *     the library never frees them.  "host" pointers are ordinary memory.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     are asynchronous on it unless they return host values, in which case
+ *     they synchronise the stream before returning.
+ *   - Inputs X are N x d row-major FP32 (point i is X[i*d .. i*d+d-1]).
+ *     Blocks of vectors (right-hand sides, solutions, MVM inputs/outputs) are
+ *     N x R column-major FP32: vector c is V[c*N .. c*N+N-1].
+ *   - Device memory: every call that needs scratch space takes it from the
+ *     context's workspace, which is allocated by gp_ctx_create / gp_ctx_reserve
+ *     and never inside a compute call.  A call whose need exceeds the
+ *     workspace returns GP_ERR_WORKSPACE; the *_workspace_size queries give
+ *     the need in advance.
+ *   - A context may be used by one host thread at a time.
+ *   - Device-side waits in the kernels are bounded; a wait that runs out sets
+ *     the context's device error word, reported as GP_ERR_TIMEOUT by the next
+ *     call that checks it (gp_ctx_check, and every call returning host values).
+ */
+#ifndef GPK_H
+#define GPK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GPK_API __attribute__((visibility("default")))
+#else
+#define GPK_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define GP_OK                  0
+#define GP_ERR_INVALID        -1  /* argument out of range / inconsistent      */
+#define GP_ERR_CUDA           -2  /* CUDA runtime or driver call failed        */
+#define GP_ERR_WORKSPACE      -3  /* context workspace smaller than required   */
+#define GP_ERR_BREAKDOWN      -4  /* LSE sum <= 0: d^T K d or r^T z not > 0     */
+#define GP_ERR_NONFINITE      -5  /* NaN/Inf in an input or an iterate          */
+#define GP_ERR_NOT_CONVERGED  -6  /* CG hit max_iter; solution and stats valid  */
+#define GP_ERR_TIMEOUT        -7  /* a bounded device-side wait ran out         */
+#define GP_ERR_OOM            -8  /* allocation refused (create/reserve only)   */
+#define GP_ERR_UNSUPPORTED    -9  /* shape or option not supported             */
+
+/* ---- kernels (k as a function of r, r^2 = sum_k (x_k - x'_k)^2 / l_k^2) -- */
+#define GP_KERNEL_RBF       0   /* exp(-r^2/2)                    App. C.1   */
+#define GP_KERNEL_MATERN32  1   /* (1 + sqrt3 r) exp(-sqrt3 r)    textbook   */
+#define GP_KERNEL_MATERN12  2   /* exp(-r)                        Sec. 3.1   */
+#define GP_KERNEL_MATERN52  3   /* (1 + sqrt5 r + 5r^2/3) exp(-sqrt5 r)      */
+
+/* ---- MVM operand precision (low byte of `flags` / gp_cg_opts_t.precision) */
+#define GP_PREC_FP32  0   /* SIMT FP32 throughout (the plain comparator)          */
+#define GP_PREC_FP16  1   /* FP16 tensor-core operands, FP32 accumulation (Sec. 4.1) */
+#define GP_PREC_BF16  2   /* BF16 tensor-core operands, FP32 accumulation          */
+
+/* ---- gp_kmvm flags (OR-ed with a GP_PREC_* value) ------------------------ */
+#define GP_MVM_ADD_NOISE     0x100  /* add sigma^2 v (needs Xr == Xc, Nr == Nc)     */
+#define GP_MVM_XSPLIT        0x200  /* hi+lo split of the scaled inputs (more exact
+                                       distances; default on for BF16)            */
+#define GP_MVM_NO_XSPLIT     0x400  /* force the split off                         */
+#define GP_MVM_SCALE_SQRT_N  0x800  /* paper-literal operand scaling v / N^{1/2}
+                                       (Sec. 4.1) instead of the per-column power
+                                       of two                                     */
+#define GP_MVM_VSPLIT       0x1000  /* FP16: carry v as hi + lo (robust to heavy
+                                       cancellation in K v; BF16 always does)     */
+#define GP_MVM_BF16_SINGLE  0x2000  /* BF16: single-term kernel tile and v (faster,
+                                       ~2^-8 rounding; the default carries both as
+                                       hi + lo so the MVM meets 2e-3)             */
+
+/* GP hyperparameters theta = (l_1..l_d, a^2, sigma^2)   (Sec. 2.2, Eq. mvm) */
+typedef struct {
+    int kernel;                 /* GP_KERNEL_*                                   */
+    int d;                      /* input dimension, 1..64                       */
+    const float* lengthscale;   /* host [d], all > 0                            */
+    double outputscale;         /* a^2 > 0                                      */
+    double noise;               /* sigma^2 >= 0 (> 0 for solves)                */
+} gp_hyp_t;
+
+typedef struct gp_ctx gp_ctx;
+
+/* Create a context on CUDA device `device` with `workspace_bytes` of device
+ * scratch memory (may be 0 and grown later with gp_ctx_reserve).  Allocates. */
+GPK_API int gp_ctx_create(int device, size_t workspace_bytes, gp_ctx** out);
+/* Free the context and its workspace.  NULL is accepted. */
+GPK_API void gp_ctx_destroy(gp_ctx* ctx);
+/* Grow the workspace to at least `workspace_bytes` (synchronises the device;
+ * allocates).  Never shrinks. */
+GPK_API int gp_ctx_reserve(gp_ctx* ctx, size_t workspace_bytes);
+/* Current workspace size in bytes. */
+GPK_API size_t gp_ctx_workspace_bytes(const gp_ctx* ctx);
+/* Synchronise `stream`, read and clear the device error word; returns
+ * GP_ERR_TIMEOUT (or another GP_ERR_*) if a kernel recorded one. */
+GPK_API int gp_ctx_check(gp_ctx* ctx, void* stream);
+/* Number of kernels this context has launched since creation (all entry
+ * points; each CUDA kernel launch counts one). */
+GPK_API int64_t gp_ctx_launch_count(const gp_ctx* ctx);
+/* Static description of a status code. */
+GPK_API const char* gp_strerror(int status);
+
+/* ---- S1+S2: matrix-free kernel MVM (Eq. mvm, Sec. 4.1) --------------------
+ *   out[:, c] = a^2 K(Xr, Xc) V[:, c]  (+ sigma^2 V[:, c] with GP_MVM_ADD_NOISE)
+ * K is never stored: 128 x 128 tiles of the kernel matrix are formed on chip
+ * (distance contraction on tensor cores, kernel function on the special
+ * function units) and contracted with V at once, block sums in FP32
+ * (Sec. 4.1, "block summation in a higher precision").
+ *   Xr   device, Nr x d row-major FP32      Xc   device, Nc x d row-major FP32
+ *   V    device, Nc x R column-major FP32   out  device, Nr x R column-major FP32
+ *   R    1..64 right-hand sides (more: call per block of 64)
+ *   flags  GP_PREC_* | GP_MVM_*
+ * Nr, Nc >= 1; Nc <= 2^31 - 128.  out must not alias V.
+ * Errors: GP_ERR_INVALID (shape/flags), GP_ERR_WORKSPACE, GP_ERR_CUDA. */
+GPK_API size_t gp_kmvm_workspace_size(const gp_hyp_t* hyp, int64_t Nr, int64_t Nc, int R, int flags);
+GPK_API int gp_kmvm(gp_ctx* ctx, const gp_hyp_t* hyp,
+            const float* Xr, int64_t Nr, const float* Xc, int64_t Nc,
+            const float* V, int R, float* out, int flags, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPK_H */

@@ -1,0 +1,195 @@
+// Internal declarations shared by the translation units of libgpk.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/gpk.h"
+
+namespace gpk {
+
+// ----------------------------------------------------------------------------
+// Host-side context
+// ----------------------------------------------------------------------------
+struct Ctx {
+    int device = 0;
+    int num_sms = 0;
+    void* ws = nullptr;           // device workspace
+    size_t ws_bytes = 0;
+    int* dev_err = nullptr;       // device error word (own allocation, 64 B)
+    int* host_pinned = nullptr;   // pinned host scratch (flags, small readbacks), 4 KB
+    int64_t launches = 0;         // kernels launched through this context
+};
+
+// Bump allocator over the context workspace (alignment 256 B).
+struct WsCarver {
+    uint8_t* base;
+    size_t cap;
+    size_t off = 0;
+    bool ok = true;
+    WsCarver(void* b, size_t c) : base((uint8_t*)b), cap(c) {}
+    template <class T> T* take(size_t count) {
+        size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+        if (off + bytes > cap) { ok = false; return nullptr; }
+        T* p = (T*)(base + off);
+        off += bytes;
+        return p;
+    }
+};
+// Size-only variant of the carver (for *_workspace_size queries).
+struct WsCounter {
+    size_t off = 0;
+    template <class T> void take(size_t count) { off += (count * sizeof(T) + 255) & ~size_t(255); }
+};
+
+#define GPK_CUDA_TRY(expr)                                   \
+    do {                                                     \
+        cudaError_t e__ = (expr);                            \
+        if (e__ != cudaSuccess) return GP_ERR_CUDA;          \
+    } while (0)
+
+#define GPK_TRY(expr)                                        \
+    do {                                                     \
+        int s__ = (expr);                                    \
+        if (s__ != GP_OK) return s__;                        \
+    } while (0)
+
+// Device error word codes (written by kernels with atomicCAS from 0).
+enum DevErr : int {
+    DEV_OK = 0,
+    DEV_TIMEOUT = 1,      // bounded mbarrier wait ran out
+    DEV_NONFINITE = 2,    // non-finite operand scale
+    DEV_BREAKDOWN = 3,
+};
+
+// Wait limit for device-side spins (nanoseconds of %globaltimer).
+constexpr uint64_t kWaitLimitNs = 1000000000ull;   // 1 s
+
+// ----------------------------------------------------------------------------
+// Operand preparation (S1): scaled inputs, norms, V scaling / casting.
+// ----------------------------------------------------------------------------
+struct OperandLayout {
+    int prec = 0;    // GP_PREC_FP16 / GP_PREC_BF16
+    int xsplit = 0;  // 1: inputs carried as hi + lo
+    int nt = 0;      // number of terms carrying t = -|x|^2/2
+    int kdim = 0;    // used columns of the contraction dimension
+    int k_pad = 0;   // 16, 32 or 64 (0: does not fit)
+    int vsplit = 0;  // 1: right-hand sides carried as hi + lo (extra P.V product)
+    int psplit = 0;  // 1: kernel tile carried as hi + lo (extra P.V product; BF16)
+};
+OperandLayout make_layout(int d, int prec, int xsplit, int vsplit, int psplit);
+float kernel_input_scale(int kernel);   // c such that x_hat = c x / l
+
+// Per-dimension input scales c / l_k, passed to kernels by value.
+struct ScaleVec {
+    float v[64];
+};
+
+// Launchers (return GP_OK or GP_ERR_CUDA).  All on `stream`.
+// XA / XB may be null (that side is not written).
+// bb: bounding box from launch_bbox (the inputs are centred on its midpoint,
+// which leaves a stationary kernel unchanged and keeps |x^| small).
+int launch_prep_x(Ctx* ctx, const OperandLayout& L, const float* X, int64_t N, int64_t N_pad, int d,
+                  const ScaleVec& inv, const unsigned* bb, void* XA, void* XB, cudaStream_t s);
+// Per-dimension min / max of X (N x d) as order-preserving integer codes:
+// bb[k] = min, bb[d + k] = max.  Deterministic (atomic min / max).
+int launch_bbox(Ctx* ctx, const float* X, int64_t N, int d, unsigned* bb, cudaStream_t s);
+int launch_prep_x_f32(Ctx* ctx, const float* X, int64_t N, int64_t N_pad, int d, int dp, const ScaleVec& inv,
+                      float* Xs, cudaStream_t s);
+int launch_v_colmax(Ctx* ctx, const float* V, int64_t N, int R, unsigned* cmax_bits, cudaStream_t s);
+// Vt rows: [0, R_pad) the (hi) cast, [R_pad, 2 R_pad) the lo parts when vsplit.
+int launch_v_cast(Ctx* ctx, int prec, int scale_mode, int vsplit, const float* V, int64_t N, int64_t N_pad, int R,
+                  int R_pad, const unsigned* cmax_bits, double outputscale, void* Vt, float* outscale,
+                  cudaStream_t s);
+
+// ----------------------------------------------------------------------------
+// MVM engines (S2)
+// ----------------------------------------------------------------------------
+struct MvmArgs {
+    int kernel;
+    int64_t Nr, Nc;
+    int R;
+    float noise;               // sigma^2 added as noise * Vnoise (0: none)
+    const float* Vnoise;       // FP32 V for the noise term (Nc x R col-major) or null
+    float* out;                // Nr x R col-major
+    int64_t ld_out;
+};
+
+// Tensor-core engine (kmvm_tc.cu).
+struct TcPlan {
+    int n_it = 0, n_jt = 0, n_split = 1, grid = 0, R_pad = 0, k_pad = 0;
+    int64_t Nr_pad = 0, Nc_pad = 0;
+};
+TcPlan tc_plan(const Ctx* ctx, int64_t Nr, int64_t Nc, int R, int k_pad);
+int tc_smem_bytes(int k_pad, int R_pad, int vsplit);
+int tc_stages(int k_pad, int R_pad, int vsplit);
+size_t tc_partial_floats(const TcPlan& p);
+int launch_kmvm_tc(Ctx* ctx, const TcPlan& plan, const OperandLayout& L, const MvmArgs& a, const CUtensorMap& tmA,
+                   const CUtensorMap& tmB, const CUtensorMap& tmV, const float* outscale, float* partial,
+                   cudaStream_t s);
+
+// SIMT FP32 engine (kmvm_simt.cu).  Scaled FP32 inputs with row stride dp.
+struct SimtPlan {
+    int dp = 0, R_pad = 0, n_rowblk = 0, n_split = 1;
+};
+SimtPlan simt_plan(const Ctx* ctx, int64_t Nr, int64_t Nc, int d, int R);
+size_t simt_partial_floats(const SimtPlan& p, int64_t Nr);
+int launch_kmvm_simt(Ctx* ctx, const SimtPlan& plan, const MvmArgs& a, float outputscale, const float* Xrs,
+                     const float* Xcs, const float* V, float* partial, cudaStream_t s);
+
+// out[c][i] = scale_c * sum_s partial[s][c][i] + noise * Vnoise[c][i], with
+// partial laid out [n_split][RP][ld_part]; scale_c = outscale[c] or outscale_const.
+int launch_split_reduce(Ctx* ctx, const float* partial, int n_split, int64_t ld_part, int64_t Nr, int R, int RP,
+                        const float* outscale, float outscale_const, float noise, const float* Vnoise,
+                        int64_t ld_v, float* out, int64_t ld_out, cudaStream_t s);
+
+// Prepared kernel-MVM operator (mvm.cu): the input side is prepared once,
+// every apply casts V and runs the engine.
+struct KOp {
+    int kernel = 0, prec = 0, flags = 0, d = 0, R_max = 0;
+    int64_t Nr = 0, Nc = 0;
+    float a2 = 1.0f, noise = 0.0f;
+    OperandLayout lay;
+    TcPlan tp;
+    SimtPlan sp;
+    void* XA = nullptr;
+    void* XB = nullptr;
+    float* Xs_r = nullptr;
+    float* Xs_c = nullptr;
+    void* Vt = nullptr;
+    float* outscale = nullptr;
+    unsigned* cmax = nullptr;
+    unsigned* bbox = nullptr;
+    float* partial = nullptr;
+    CUtensorMap tmA, tmB, tmV;
+};
+size_t kop_workspace(const Ctx* ctx, const gp_hyp_t* hyp, int64_t Nr, int64_t Nc, int R, int flags, bool square);
+int kop_prepare(Ctx* ctx, WsCarver& wc, KOp& op, const gp_hyp_t* hyp, const float* Xr, int64_t Nr,
+                const float* Xc, int64_t Nc, int R, int flags, cudaStream_t s);
+// out = K(Xr, Xc) V (+ sigma^2 V if add_noise); V: Nc x R (ld Nc), out: Nr x R (ld ld_out).
+int kop_apply(Ctx* ctx, KOp& op, const float* V, int R, float* out, int64_t ld_out, bool add_noise, cudaStream_t s);
+
+// Tensor-map helper (driver entry point fetched through the runtime).
+int encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uint64_t inner, uint64_t outer,
+                   uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle swz);
+
+// Hyperparameter validation shared by the entry points.
+int check_hyp(const gp_hyp_t* hyp);
+
+// ---- preconditioner (precond.cu) ----
+size_t pivchol_workspace(const Ctx* ctx, int64_t N, int d, int rank);
+int pivchol_run(Ctx* ctx, WsCarver& wc, const gp_hyp_t* hyp, const float* X, int64_t N, int rank, float* L,
+                int32_t* piv, double* core, int* rank_out_host, cudaStream_t s);
+size_t woodbury_workspace(const Ctx* ctx, int64_t N, int k, int R);
+// Z = P^{-1} W on the active columns (active may be null = all).
+int woodbury_apply(Ctx* ctx, WsCarver& wc, const float* L, const double* core, int k, double noise, int64_t N,
+                   const float* W, int R, const int* active, float* Z, cudaStream_t s);
+
+}  // namespace gpk
+
+// The opaque handle of the C ABI is the context itself.
+struct gp_ctx : public gpk::Ctx {};

@@ -1,0 +1,483 @@
+// S2: the tensor-core kernel MVM (Eq. mvm; Sec. 4.1).
+//
+//   out_i = a^2 sum_j k(x_i, x_j) v_j (+ sigma^2 v_i)
+//
+// One CTA owns a 128-row tile of the output and streams 128-column tiles of
+// the kernel matrix, which never leaves the chip ("matrix-free"):
+//   1. TMA brings the column tile's operand rows XB_j (128 x K) and the cast
+//      right-hand sides Vt_j (R_pad x 128) into a 4-stage shared-memory ring.
+//   2. One thread issues S = XA_i XB_j^T (tcgen05.mma kind::f16, M=N=128,
+//      K = 16/32/64) into a TMEM buffer; with the norm terms folded into the
+//      contraction dimension S is already s_ij = -c^2 r_ij^2 / 2.
+//   3. An epilogue warpgroup reads its S rows from TMEM (one row per
+//      thread), evaluates the kernel function on the special function units,
+//      rounds the tile to FP16/BF16 and writes it back into the same TMEM
+//      columns as P.
+//   4. The MMA thread issues O += P Vt_j^T with P taken from TMEM
+//      (M = 128, N = R_pad, K = 128), accumulating in FP32 in TMEM.  This is
+//      the paper's block summation in higher precision, with 128 x 128 blocks.
+// Two S buffers and two epilogue warpgroups alternate so that the special
+// function units (the roofline of this kernel) stay busy while the tensor
+// core works on the other buffer.  After the last column tile, warpgroup 0
+// reads O and writes a^2 O / s_c (+ sigma^2 v) -- or the raw partial when the
+// column range is split across CTAs -- straight to global memory.
+//
+// Warp roles (320 threads): warps 0-3 epilogue WG0, 4-7 epilogue WG1,
+// warp 8 TMA producer, warp 9 MMA issuer + TMEM owner.  Persistent CTAs walk
+// the (row tile, column split) work items round-robin.  Every mbarrier wait is
+// bounded; a wait that runs out records DEV_TIMEOUT in the device error word,
+// drains the asynchronous copies / MMAs it issued, frees TMEM and exits.
+#include "gpk_internal.cuh"
+#include "ptx.cuh"
+#include "kfun.cuh"
+
+namespace gpk {
+
+namespace {
+
+constexpr int kBM = 128;
+constexpr int kBN = 128;
+constexpr int kStages = 4;
+constexpr int kThreads = 320;
+constexpr int kTmaWarp = 8;
+constexpr int kMmaWarp = 9;
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kOCol = 256;          // O accumulator columns [256, 256 + R_pad), R_pad <= 64
+constexpr uint32_t kPLoCol = 320;        // lo parts of the kernel tile (split mode): [320 + 64 b, +64)
+constexpr int kMinSmemBytes = 120 * 1024; // keeps one CTA per SM (TMEM is taken whole)
+constexpr int kMaxSmemBytes = 227 * 1024; // opt-in maximum per CTA
+
+struct TcParams {
+    int n_it, n_jt, n_split, n_items;
+    int k_pad, R_pad, R;
+    int vsplit;                  // 1: Vt carries hi rows then lo rows
+    int psplit;                  // 1: the kernel tile is carried as hi (in place) + lo (kPLoCol)
+    int stages;                  // shared-memory ring depth (<= kStages)
+    int64_t Nr;
+    float noise;                 // sigma^2, 0 = no noise term
+    const float* Vnoise;         // FP32 V (ld = ld_v) for the noise term
+    int64_t ld_v;
+    const float* outscale;       // [R_pad] a^2 / s_c
+    float* out;                  // Nr x R col-major (ld_out)
+    int64_t ld_out;
+    float* partial;              // [n_split][R_pad][ld_part] when n_split > 1
+    int64_t ld_part;
+    int* err;
+    uint64_t limit_ns;
+};
+
+struct TcBarriers {
+    uint64_t full[kStages];
+    uint64_t empty[kStages];
+    uint64_t s_full[2];
+    uint64_t p_full[2];
+    uint64_t o_full;
+    uint64_t o_empty;
+    uint64_t xi_full;
+    uint64_t xi_empty;
+    uint64_t drain;
+};
+
+__device__ __forceinline__ void record_error(int* err, int code) { atomicCAS(err, 0, code); }
+
+__device__ __forceinline__ void item_range(const TcParams& p, int item, int& it, int& j0, int& j1) {
+    it = item % p.n_it;
+    const int sp = item / p.n_it;
+    j0 = (int)(((int64_t)sp * p.n_jt) / p.n_split);
+    j1 = (int)(((int64_t)(sp + 1) * p.n_jt) / p.n_split);
+}
+
+// ---- TMA producer (one thread) ------------------------------------------------
+__device__ void tc_producer(const TcParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB,
+                            const CUtensorMap* tmV, TcBarriers& bars, uint8_t* sXi, uint8_t* sSt,
+                            uint32_t xbytes, uint32_t vbytes) {
+    uint32_t fills = 0, xi_loads = 0;
+    bool ok = true;
+    int ic = 0;
+    const uint32_t S = (uint32_t)p.stages;
+    const int natoms = p.k_pad > 64 ? p.k_pad / 64 : 1;
+    const uint32_t abytes = xbytes / natoms;
+    for (int item = blockIdx.x; item < p.n_items; item += gridDim.x, ++ic) {
+        int it, j0, j1;
+        item_range(p, item, it, j0, j1);
+        if (ic > 0 && !ptx::mbar_wait(&bars.xi_empty, (ic - 1) & 1, p.limit_ns)) { ok = false; break; }
+        ptx::mbar_arrive_expect_tx(&bars.xi_full, xbytes);
+        for (int a = 0; a < natoms; ++a)
+            ptx::tma_load_2d(sXi + a * abytes, tmA, &bars.xi_full, a * 64, it * kBM);
+        ++xi_loads;
+        for (int jt = j0; jt < j1; ++jt) {
+            const uint32_t st = fills % S, u = fills / S;
+            if (u > 0 && !ptx::mbar_wait(&bars.empty[st], (u - 1) & 1, p.limit_ns)) { ok = false; break; }
+            uint8_t* sx = sSt + st * (xbytes + vbytes);
+            ptx::mbar_arrive_expect_tx(&bars.full[st], xbytes + vbytes);
+            for (int a = 0; a < natoms; ++a) ptx::tma_load_2d(sx + a * abytes, tmB, &bars.full[st], a * 64, jt * kBN);
+            const uint32_t vbox = (uint32_t)p.R_pad * 128u;   // one 64-column box of R_pad rows
+            for (int part = 0; part <= p.vsplit; ++part) {
+                uint8_t* sv = sx + xbytes + part * 2u * vbox;
+                ptx::tma_load_2d(sv, tmV, &bars.full[st], jt * kBN, part * p.R_pad);
+                ptx::tma_load_2d(sv + vbox, tmV, &bars.full[st], jt * kBN + 64, part * p.R_pad);
+            }
+            ++fills;
+        }
+        if (!ok) break;
+    }
+    if (!ok) {
+        record_error(p.err, DEV_TIMEOUT);
+        // Let every copy this thread issued land before the CTA can exit.
+        const uint32_t first = fills > S ? fills - S : 0;
+        for (uint32_t f = first; f < fills; ++f) ptx::mbar_wait(&bars.full[f % S], (f / S) & 1, p.limit_ns);
+        if (xi_loads > 0) ptx::mbar_wait(&bars.xi_full, (xi_loads - 1) & 1, p.limit_ns);
+    }
+}
+
+// ---- MMA issuer (one thread) ----------------------------------------------------
+__device__ void tc_mma(const TcParams& p, TcBarriers& bars, const uint8_t* sXi, const uint8_t* sSt,
+                       uint32_t xbytes, uint32_t vbytes, uint32_t tmem, uint32_t id_s, uint32_t id_pv) {
+    const uint32_t arow = p.k_pad * 2 < 128 ? (uint32_t)p.k_pad * 2u : 128u;  // bytes per row of one atom
+    const uint32_t swz = (arow == 32) ? 6u : (arow == 64 ? 4u : 2u);         // 32B / 64B / 128B swizzle
+    const uint32_t sbo_x = 8u * arow;                                        // 8 rows of the swizzle atom
+    const uint32_t abytes = (uint32_t)kBM * arow;                            // one atom of a 128-row tile
+    const int ksteps = p.k_pad / 16;
+    const uint32_t S = (uint32_t)p.stages;
+    const uint32_t aXi = ptx::smem_u32(sXi);
+    const uint32_t aSt = ptx::smem_u32(sSt);
+    const uint32_t stage_bytes = xbytes + vbytes;
+    uint32_t n = 0, gt = 0;
+    int ic = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x, ++ic) {
+        int it, j0, j1;
+        item_range(p, item, it, j0, j1);
+        const uint32_t T = (uint32_t)(j1 - j0);
+        if (!ptx::mbar_wait(&bars.xi_full, ic & 1, p.limit_ns)) { ok = false; break; }
+        if (ic > 0 && !ptx::mbar_wait(&bars.o_full, (ic - 1) & 1, p.limit_ns)) { ok = false; break; }
+        // (the previous item's last P.V products are complete: their TMEM
+        //  buffers may now receive this item's first S tiles)
+        ptx::tc_fence_after();
+        auto issue_s = [&](uint32_t t) -> bool {
+            const uint32_t f = n + t, st = f % S;
+            if (!ptx::mbar_wait(&bars.full[st], (f / S) & 1, p.limit_ns)) return false;
+            ptx::tc_fence_after();
+            const uint32_t b = (gt + t) & 1;
+            const uint32_t aXj = aSt + st * stage_bytes;
+            for (int kk = 0; kk < ksteps; ++kk) {
+                const uint32_t koff = ((uint32_t)kk * 32u / arow) * abytes + ((uint32_t)kk * 32u) % arow;
+                const uint64_t da = ptx::smem_desc(aXi + koff, 16, sbo_x, swz);
+                const uint64_t db = ptx::smem_desc(aXj + koff, 16, sbo_x, swz);
+                ptx::mma_f16_ss(tmem + b * 128u, da, db, id_s, kk > 0 ? 1u : 0u);
+            }
+            ptx::mma_commit(&bars.s_full[b]);
+            return true;
+        };
+        if (!issue_s(0)) { ok = false; break; }
+        if (T > 1 && !issue_s(1)) { ok = false; break; }
+        for (uint32_t t = 0; t < T; ++t) {
+            const uint32_t g = gt + t, b = g & 1;
+            if (!ptx::mbar_wait(&bars.p_full[b], (g >> 1) & 1, p.limit_ns)) { ok = false; break; }
+            ptx::tc_fence_after();
+            if (t == 0 && ic > 0) {
+                if (!ptx::mbar_wait(&bars.o_empty, (ic - 1) & 1, p.limit_ns)) { ok = false; break; }
+                ptx::tc_fence_after();
+            }
+            const uint32_t f = n + t, st = f % S;
+            const uint32_t aV = aSt + st * stage_bytes + xbytes;
+            const uint32_t vbox = (uint32_t)p.R_pad * 128u;
+            // Products accumulated into O: P_hi V_hi, then P_hi V_lo (vsplit), then P_lo V_hi (psplit).
+            const int nprod = 1 + p.vsplit + p.psplit;
+            for (int q = 0; q < nprod; ++q) {
+                const uint32_t vpart = (q == 1 && p.vsplit) ? 1u : 0u;
+                const uint32_t pcol = (q == nprod - 1 && p.psplit && q > 0) ? (kPLoCol + b * 64u) : (b * 128u);
+                for (int kk = 0; kk < kBN / 16; ++kk) {
+                    const uint32_t atom = (uint32_t)kk >> 2, kin = (uint32_t)kk & 3u;
+                    const uint64_t dv =
+                        ptx::smem_desc(aV + (2u * vpart + atom) * vbox + kin * 32u, 16, 1024, 2u);
+                    ptx::mma_f16_ts(tmem + kOCol, tmem + pcol + (uint32_t)kk * 8u, dv, id_pv,
+                                    (t > 0 || kk > 0 || q > 0) ? 1u : 0u);
+                }
+            }
+            ptx::mma_commit(&bars.empty[st]);
+            if (t + 2 < T) {
+                // P in buffer b must be consumed before S(t+2) overwrites it.
+                if (!ptx::mbar_wait(&bars.empty[st], (f / S) & 1, p.limit_ns)) { ok = false; break; }
+                if (!issue_s(t + 2)) { ok = false; break; }
+            }
+        }
+        if (!ok) break;
+        ptx::mma_commit(&bars.o_full);
+        ptx::mma_commit(&bars.xi_empty);
+        n += T;
+        gt += T;
+    }
+    // No MMA may be in flight when TMEM is released.
+    ptx::mma_commit(&bars.drain);
+    ptx::mbar_wait(&bars.drain, 0, p.limit_ns);
+    if (!ok) record_error(p.err, DEV_TIMEOUT);
+}
+
+template <int BF16>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+    if constexpr (BF16) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<uint32_t*>(&h);
+    } else {
+        __half2 h = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<uint32_t*>(&h);
+    }
+}
+
+// ---- epilogue warpgroups ------------------------------------------------------------
+template <int BF16>
+__device__ __forceinline__ float unpack_lo(uint32_t v) {
+    if constexpr (BF16) return __uint_as_float(v << 16);
+    else return __half2float(__ushort_as_half((unsigned short)(v & 0xFFFFu)));
+}
+template <int BF16>
+__device__ __forceinline__ float unpack_hi(uint32_t v) {
+    if constexpr (BF16) return __uint_as_float(v & 0xFFFF0000u);
+    else return __half2float(__ushort_as_half((unsigned short)(v >> 16)));
+}
+
+template <int KIND, int BF16, int PSPLIT>
+__device__ void tc_epilogue(const TcParams& p, TcBarriers& bars, uint32_t tmem, int wg, int wq, int lane) {
+    const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
+    const int row = wq * 32 + lane;
+    uint32_t gt = 0;
+    int ic = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < p.n_items; item += gridDim.x, ++ic) {
+        int it, j0, j1;
+        item_range(p, item, it, j0, j1);
+        const uint32_t T = (uint32_t)(j1 - j0);
+        for (uint32_t t = 0; t < T; ++t) {
+            const uint32_t g = gt + t, b = g & 1;
+            if ((int)b != wg) continue;
+            if (!ptx::mbar_wait(&bars.s_full[b], (g >> 1) & 1, p.limit_ns)) { ok = false; break; }
+            ptx::tc_fence_after();
+            const uint32_t tS = tmem + lane_off + b * 128u;
+#pragma unroll 1
+            for (int h = 0; h < 4; ++h) {
+                uint32_t r[32];
+                ptx::tmem_ld32(tS + (uint32_t)h * 32u, r);
+                ptx::tmem_wait_ld();
+                uint32_t pk[16];
+                uint32_t pl[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const float k0 = kernel_from_s<KIND>(__uint_as_float(r[2 * e]));
+                    const float k1 = kernel_from_s<KIND>(__uint_as_float(r[2 * e + 1]));
+                    pk[e] = pack2<BF16>(k0, k1);
+                    if constexpr (PSPLIT) pl[e] = pack2<BF16>(k0 - unpack_lo<BF16>(pk[e]), k1 - unpack_hi<BF16>(pk[e]));
+                }
+                ptx::tmem_st16(tS + (uint32_t)h * 16u, pk);
+                if constexpr (PSPLIT) ptx::tmem_st16(tmem + lane_off + kPLoCol + b * 64u + (uint32_t)h * 16u, pl);
+            }
+            ptx::tmem_wait_st();
+            ptx::tc_fence_before();
+            ptx::mbar_arrive(&bars.p_full[b]);
+        }
+        if (!ok) break;
+        if (wg == 0) {
+            if (!ptx::mbar_wait(&bars.o_full, ic & 1, p.limit_ns)) { ok = false; break; }
+            ptx::tc_fence_after();
+            const int64_t i = (int64_t)it * kBM + row;
+            const int sp = item / p.n_it;
+            for (int c0 = 0; c0 < p.R_pad; c0 += 16) {
+                uint32_t o[16];
+                ptx::tmem_ld16(tmem + lane_off + kOCol + (uint32_t)c0, o);
+                ptx::tmem_wait_ld();
+                if (i < p.Nr) {
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const int c = c0 + e;
+                        if (c < p.R) {
+                            const float acc = __uint_as_float(o[e]);
+                            if (p.n_split == 1) {
+                                float val = acc * p.outscale[c];
+                                if (p.noise != 0.0f) val = fmaf(p.noise, p.Vnoise[c * p.ld_v + i], val);
+                                p.out[c * p.ld_out + i] = val;
+                            } else {
+                                p.partial[((int64_t)sp * p.R_pad + c) * p.ld_part + i] = acc;
+                            }
+                        }
+                    }
+                }
+            }
+            ptx::tc_fence_before();
+            ptx::mbar_arrive(&bars.o_empty);
+        }
+        gt += T;
+    }
+    if (!ok) record_error(p.err, DEV_TIMEOUT);
+}
+
+template <int KIND, int BF16, int PSPLIT>
+__global__ void __launch_bounds__(kThreads, 1)
+kmvm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const __grid_constant__ CUtensorMap tmV, const TcParams p) {
+    extern __shared__ uint8_t dsm[];
+    __shared__ TcBarriers bars;
+    __shared__ uint32_t tmem_slot;
+
+    uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
+    const uint32_t xbytes = (uint32_t)kBM * (uint32_t)p.k_pad * 2u;
+    const uint32_t vbytes = (uint32_t)(1 + p.vsplit) * (uint32_t)p.R_pad * (uint32_t)kBN * 2u;
+    uint8_t* sXi = base;
+    uint8_t* sSt = base + xbytes;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            ptx::mbar_init(&bars.full[s], 1);
+            ptx::mbar_init(&bars.empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            ptx::mbar_init(&bars.s_full[b], 1);
+            ptx::mbar_init(&bars.p_full[b], 128);
+        }
+        ptx::mbar_init(&bars.o_full, 1);
+        ptx::mbar_init(&bars.o_empty, 128);
+        ptx::mbar_init(&bars.xi_full, 1);
+        ptx::mbar_init(&bars.xi_empty, 1);
+        ptx::mbar_init(&bars.drain, 1);
+        ptx::fence_mbar_init();
+    }
+    if (warp == kTmaWarp && lane == 0) {
+        ptx::tma_prefetch_desc(&tmA);
+        ptx::tma_prefetch_desc(&tmB);
+        ptx::tma_prefetch_desc(&tmV);
+    }
+    if (warp == kMmaWarp) ptx::tmem_alloc(&tmem_slot, kTmemCols);
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == kTmaWarp) {
+        if (lane == 0) tc_producer(p, &tmA, &tmB, &tmV, bars, sXi, sSt, xbytes, vbytes);
+        __syncwarp();
+    } else if (warp == kMmaWarp) {
+        if (lane == 0)
+            tc_mma(p, bars, sXi, sSt, xbytes, vbytes, tmem, ptx::idesc_f16(kBM, kBN, BF16),
+                   ptx::idesc_f16(kBM, p.R_pad, BF16));
+        __syncwarp();
+    } else {
+        tc_epilogue<KIND, BF16, PSPLIT>(p, bars, tmem, warp >> 2, warp & 3, lane);
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    if (warp == kMmaWarp) ptx::tmem_dealloc(tmem, kTmemCols);
+}
+
+template <int KIND, int BF16, int PSPLIT>
+cudaError_t launch_tc_typed(const TcPlan& plan, const TcParams& prm, const CUtensorMap& a, const CUtensorMap& b,
+                            const CUtensorMap& v, cudaStream_t s) {
+    const int smem = tc_smem_bytes(plan.k_pad, plan.R_pad, prm.vsplit);
+    auto kfn = kmvm_tc_kernel<KIND, BF16, PSPLIT>;
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kfn<<<plan.grid, kThreads, smem, s>>>(a, b, v, prm);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int tc_stages(int k_pad, int R_pad, int vsplit) {
+    const int xbytes = kBM * k_pad * 2;
+    const int vbytes = (1 + vsplit) * R_pad * kBN * 2;
+    for (int st = kStages; st >= 2; --st)
+        if (1024 + xbytes + st * (xbytes + vbytes) <= kMaxSmemBytes) return st;
+    return 0;
+}
+
+int tc_smem_bytes(int k_pad, int R_pad, int vsplit) {
+    const int xbytes = kBM * k_pad * 2;
+    const int vbytes = (1 + vsplit) * R_pad * kBN * 2;
+    int need = 1024 + xbytes + tc_stages(k_pad, R_pad, vsplit) * (xbytes + vbytes);
+    return need < kMinSmemBytes ? kMinSmemBytes : need;
+}
+
+TcPlan tc_plan(const Ctx* ctx, int64_t Nr, int64_t Nc, int R, int k_pad) {
+    TcPlan p;
+    p.k_pad = k_pad;
+    p.R_pad = ((R + 15) / 16) * 16;
+    p.n_it = (int)((Nr + kBM - 1) / kBM);
+    p.n_jt = (int)((Nc + kBN - 1) / kBN);
+    p.Nr_pad = (int64_t)p.n_it * kBM;
+    p.Nc_pad = (int64_t)p.n_jt * kBN;
+    const int G = ctx->num_sms > 0 ? ctx->num_sms : 1;
+    // Pick the column split minimising the busiest CTA's work: waves x tiles
+    // per item, plus a fixed per-item cost (pipeline fill, O read-out) of about
+    // two tiles, plus the partial-sum reduction when split.
+    int best = 1;
+    double best_cost = 1e300;
+    const int max_split = p.n_jt < 16 ? p.n_jt : 16;
+    for (int sp = 1; sp <= max_split; ++sp) {
+        const int64_t items = (int64_t)p.n_it * sp;
+        const int64_t waves = (items + G - 1) / G;
+        const int64_t tiles = (p.n_jt + sp - 1) / sp;
+        double cost = (double)waves * (double)(tiles + 2);
+        if (sp > 1) cost += 0.05 * (double)sp * (double)p.n_it * (double)p.R_pad / (double)G / 64.0;
+        if (cost < best_cost - 1e-9) { best_cost = cost; best = sp; }
+    }
+    p.n_split = best;
+    const int64_t items = (int64_t)p.n_it * p.n_split;
+    p.grid = (int)(items < G ? items : G);
+    return p;
+}
+
+size_t tc_partial_floats(const TcPlan& p) {
+    return p.n_split > 1 ? (size_t)p.n_split * p.R_pad * p.Nr_pad : 0;
+}
+
+int launch_kmvm_tc(Ctx* ctx, const TcPlan& plan, const OperandLayout& L, const MvmArgs& a, const CUtensorMap& tmA,
+                   const CUtensorMap& tmB, const CUtensorMap& tmV, const float* outscale, float* partial,
+                   cudaStream_t s) {
+    TcParams prm;
+    prm.n_it = plan.n_it;
+    prm.n_jt = plan.n_jt;
+    prm.n_split = plan.n_split;
+    prm.n_items = plan.n_it * plan.n_split;
+    prm.k_pad = plan.k_pad;
+    prm.R_pad = plan.R_pad;
+    prm.R = a.R;
+    prm.vsplit = L.vsplit;
+    prm.psplit = L.psplit;
+    prm.stages = tc_stages(plan.k_pad, plan.R_pad, L.vsplit);
+    if (prm.stages < 2) return GP_ERR_UNSUPPORTED;
+    prm.Nr = a.Nr;
+    prm.noise = a.noise;
+    prm.Vnoise = a.Vnoise;
+    prm.ld_v = a.Nc;
+    prm.outscale = outscale;
+    prm.out = a.out;
+    prm.ld_out = a.ld_out;
+    prm.partial = partial;
+    prm.ld_part = plan.Nr_pad;
+    prm.err = ctx->dev_err;
+    prm.limit_ns = kWaitLimitNs;
+    const int bf = (L.prec == GP_PREC_BF16) ? 1 : 0;
+    cudaError_t e = cudaErrorInvalidValue;
+#define GPK_TC_CASE(K)                                                                  \
+    case K:                                                                             \
+        e = bf ? (L.psplit ? launch_tc_typed<K, 1, 1>(plan, prm, tmA, tmB, tmV, s)      \
+                           : launch_tc_typed<K, 1, 0>(plan, prm, tmA, tmB, tmV, s))     \
+               : launch_tc_typed<K, 0, 0>(plan, prm, tmA, tmB, tmV, s);                 \
+        break;
+    switch (a.kernel) {
+        GPK_TC_CASE(GP_KERNEL_RBF)
+        GPK_TC_CASE(GP_KERNEL_MATERN32)
+        GPK_TC_CASE(GP_KERNEL_MATERN12)
+        GPK_TC_CASE(GP_KERNEL_MATERN52)
+        default: return GP_ERR_INVALID;
+    }
+#undef GPK_TC_CASE
+    ctx->launches++;
+    if (e != cudaSuccess) return GP_ERR_CUDA;
+    if (plan.n_split > 1)
+        return launch_split_reduce(ctx, partial, plan.n_split, plan.Nr_pad, a.Nr, a.R, plan.R_pad, outscale, 0.0f,
+                                   a.noise, a.Vnoise, a.Nc, a.out, a.ld_out, s);
+    return GP_OK;
+}
+
+}  // namespace gpk

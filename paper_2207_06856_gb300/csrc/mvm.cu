@@ -1,0 +1,194 @@
+// Kernel-MVM operator: prepares the input-side operands once (S1) and applies
+// K(Xr, Xc) V (+ sigma^2 V) any number of times (S2).  Used by gp_kmvm and by
+// every solver, so the MVM inside CG is exactly the MVM that gp_kmvm exposes.
+#include "gpk_internal.cuh"
+
+#include <math.h>
+#include <string.h>
+
+namespace gpk {
+
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+CUtensorMapSwizzle swizzle_for_row_bytes(uint32_t row_bytes) {
+    return row_bytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
+                           : (row_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B);
+}
+// Rows wider than 128 bytes are loaded as several 128-byte swizzle atoms.
+uint32_t atom_row_bytes(int k_pad) { return (uint32_t)(k_pad * 2 < 128 ? k_pad * 2 : 128); }
+
+}  // namespace
+
+int encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uint64_t inner, uint64_t outer,
+                   uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle swz) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return GP_ERR_CUDA;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {row_bytes};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? GP_OK : GP_ERR_CUDA;
+}
+
+// Allocation plan of a KOp, shared by the size query and the real carve so the
+// two can never disagree.
+template <class A>
+static void kop_layout(A& a, KOp& op, int64_t Nr, int64_t Nc, int R_max, bool square) {
+    if (op.prec == GP_PREC_FP32) {
+        a.template take<float>((size_t)Nr * op.sp.dp);
+        if (!square) a.template take<float>((size_t)Nc * op.sp.dp);
+        a.template take<float>(simt_partial_floats(op.sp, Nr));
+    } else {
+        a.template take<uint16_t>((size_t)op.tp.Nr_pad * op.lay.k_pad);
+        a.template take<uint16_t>((size_t)op.tp.Nc_pad * op.lay.k_pad);
+        const int rp = ((R_max + 15) / 16) * 16;
+        a.template take<uint16_t>((size_t)(op.lay.vsplit ? 2 : 1) * rp * op.tp.Nc_pad);
+        a.template take<float>(64);
+        a.template take<unsigned>(64);
+        a.template take<unsigned>(128);
+        a.template take<float>((size_t)op.tp.n_split * rp * op.tp.Nr_pad);
+    }
+}
+
+static int kop_plan(const Ctx* ctx, KOp& op, const gp_hyp_t* hyp, int64_t Nr, int64_t Nc, int R, int flags) {
+    op.kernel = hyp->kernel;
+    op.d = hyp->d;
+    op.prec = flags & 0xff;
+    op.flags = flags;
+    op.Nr = Nr;
+    op.Nc = Nc;
+    op.a2 = (float)hyp->outputscale;
+    op.noise = (float)hyp->noise;
+    op.R_max = R;
+    if (op.prec == GP_PREC_FP32) {
+        op.sp = simt_plan(ctx, Nr, Nc, hyp->d, R < 32 ? R : 32);
+    } else if (op.prec == GP_PREC_FP16 || op.prec == GP_PREC_BF16) {
+        const bool bf = op.prec == GP_PREC_BF16;
+        // Inputs carried as hi + lo by default for BF16 (8-bit significand) and
+        // for FP16 beyond 12 dimensions, where one rounding of |x^| ~ sqrt(d)
+        // moves the distances by a relative 2^-12 sqrt(d).
+        int xsplit = (flags & GP_MVM_XSPLIT) ? 1 : 0;
+        if (!(flags & GP_MVM_NO_XSPLIT) && (bf || hyp->d > 12)) xsplit = 1;
+        if (flags & GP_MVM_NO_XSPLIT) xsplit = 0;
+        if (xsplit && make_layout(hyp->d, op.prec, 1, 0, 0).k_pad == 0) xsplit = 0;   // does not fit
+        const int single = (flags & GP_MVM_BF16_SINGLE) ? 1 : 0;
+        const int vsplit = bf ? !single : ((flags & GP_MVM_VSPLIT) ? 1 : 0);
+        const int psplit = bf ? !single : 0;
+        op.lay = make_layout(hyp->d, op.prec, xsplit, vsplit, psplit);
+        if (op.lay.k_pad == 0) return GP_ERR_UNSUPPORTED;
+        op.tp = tc_plan(ctx, Nr, Nc, R < 64 ? R : 64, op.lay.k_pad);
+    } else {
+        return GP_ERR_INVALID;
+    }
+    return GP_OK;
+}
+
+size_t kop_workspace(const Ctx* ctx, const gp_hyp_t* hyp, int64_t Nr, int64_t Nc, int R, int flags, bool square) {
+    KOp op;
+    if (kop_plan(ctx, op, hyp, Nr, Nc, R, flags) != GP_OK) return 0;
+    WsCounter c;
+    kop_layout(c, op, Nr, Nc, R, square);
+    return c.off;
+}
+
+int kop_prepare(Ctx* ctx, WsCarver& wc, KOp& op, const gp_hyp_t* hyp, const float* Xr, int64_t Nr,
+                const float* Xc, int64_t Nc, int R, int flags, cudaStream_t s) {
+    GPK_TRY(kop_plan(ctx, op, hyp, Nr, Nc, R, flags));
+    const bool square = (Xr == Xc && Nr == Nc);
+    ScaleVec inv;
+    memset(&inv, 0, sizeof(inv));
+    const float c = kernel_input_scale(hyp->kernel);
+    if (op.prec == GP_PREC_FP32) {
+        // SIMT engine: q = |x^_i - x^_j|^2 with x^ = (c / sqrt2) x / l, so s = -q.
+        for (int k = 0; k < hyp->d; ++k) inv.v[k] = (float)((double)c / sqrt(2.0) / (double)hyp->lengthscale[k]);
+        op.Xs_r = wc.take<float>((size_t)Nr * op.sp.dp);
+        op.Xs_c = square ? op.Xs_r : wc.take<float>((size_t)Nc * op.sp.dp);
+        op.partial = wc.take<float>(simt_partial_floats(op.sp, Nr));
+        if (!wc.ok) return GP_ERR_WORKSPACE;
+        GPK_TRY(launch_prep_x_f32(ctx, Xr, Nr, Nr, hyp->d, op.sp.dp, inv, op.Xs_r, s));
+        if (!square) GPK_TRY(launch_prep_x_f32(ctx, Xc, Nc, Nc, hyp->d, op.sp.dp, inv, op.Xs_c, s));
+        return GP_OK;
+    }
+    for (int k = 0; k < hyp->d; ++k) inv.v[k] = (float)((double)c / (double)hyp->lengthscale[k]);
+    op.XA = wc.take<uint16_t>((size_t)op.tp.Nr_pad * op.lay.k_pad);
+    op.XB = wc.take<uint16_t>((size_t)op.tp.Nc_pad * op.lay.k_pad);
+    const int rp = ((op.R_max + 15) / 16) * 16;
+    op.Vt = wc.take<uint16_t>((size_t)(op.lay.vsplit ? 2 : 1) * rp * op.tp.Nc_pad);
+    op.outscale = wc.take<float>(64);
+    op.cmax = wc.take<unsigned>(64);
+    op.bbox = wc.take<unsigned>(128);
+    op.partial = wc.take<float>((size_t)op.tp.n_split * rp * op.tp.Nr_pad);
+    if (!wc.ok) return GP_ERR_WORKSPACE;
+    GPK_TRY(launch_bbox(ctx, Xc, Nc, hyp->d, op.bbox, s));
+    if (square) {
+        GPK_TRY(launch_prep_x(ctx, op.lay, Xr, Nr, op.tp.Nr_pad, hyp->d, inv, op.bbox, op.XA, op.XB, s));
+    } else {
+        GPK_TRY(launch_prep_x(ctx, op.lay, Xr, Nr, op.tp.Nr_pad, hyp->d, inv, op.bbox, op.XA, nullptr, s));
+        GPK_TRY(launch_prep_x(ctx, op.lay, Xc, Nc, op.tp.Nc_pad, hyp->d, inv, op.bbox, nullptr, op.XB, s));
+    }
+    const CUtensorMapDataType dt =
+        op.prec == GP_PREC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const uint32_t rowb = (uint32_t)op.lay.k_pad * 2u;
+    const uint32_t arb = atom_row_bytes(op.lay.k_pad);
+    GPK_TRY(encode_tmap_2d(&op.tmA, dt, op.XA, op.lay.k_pad, op.tp.Nr_pad, rowb, arb / 2, 128,
+                           swizzle_for_row_bytes(arb)));
+    GPK_TRY(encode_tmap_2d(&op.tmB, dt, op.XB, op.lay.k_pad, op.tp.Nc_pad, rowb, arb / 2, 128,
+                           swizzle_for_row_bytes(arb)));
+    return GP_OK;
+}
+
+int kop_apply(Ctx* ctx, KOp& op, const float* V, int R, float* out, int64_t ld_out, bool add_noise, cudaStream_t s) {
+    if (R > op.R_max) return GP_ERR_INVALID;
+    const int maxc = op.prec == GP_PREC_FP32 ? 32 : 64;
+    for (int c0 = 0; c0 < R; c0 += maxc) {
+        const int rc = (R - c0) < maxc ? (R - c0) : maxc;
+        MvmArgs a;
+        a.kernel = op.kernel;
+        a.Nr = op.Nr;
+        a.Nc = op.Nc;
+        a.R = rc;
+        a.noise = add_noise ? op.noise : 0.0f;
+        a.Vnoise = V + (int64_t)c0 * op.Nc;
+        a.out = out + (int64_t)c0 * ld_out;
+        a.ld_out = ld_out;
+        const float* Vc = V + (int64_t)c0 * op.Nc;
+        if (op.prec == GP_PREC_FP32) {
+            SimtPlan pl = op.sp;
+            pl.R_pad = rc <= 4 ? 4 : (rc <= 8 ? 8 : (rc <= 16 ? 16 : 32));
+            GPK_TRY(launch_kmvm_simt(ctx, pl, a, op.a2, op.Xs_r, op.Xs_c, Vc, op.partial, s));
+        } else {
+            TcPlan pl = op.tp;
+            pl.R_pad = ((rc + 15) / 16) * 16;
+            GPK_TRY(launch_v_colmax(ctx, Vc, op.Nc, rc, op.cmax, s));
+            GPK_TRY(launch_v_cast(ctx, op.prec, (op.flags & GP_MVM_SCALE_SQRT_N) ? 1 : 0, op.lay.vsplit, Vc, op.Nc,
+                                  pl.Nc_pad, rc, pl.R_pad, op.cmax, op.a2, op.Vt, op.outscale, s));
+            const CUtensorMapDataType dt =
+                op.prec == GP_PREC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+            GPK_TRY(encode_tmap_2d(&op.tmV, dt, op.Vt, pl.Nc_pad, (uint64_t)(op.lay.vsplit ? 2 : 1) * pl.R_pad,
+                                   pl.Nc_pad * 2, 64, pl.R_pad, CU_TENSOR_MAP_SWIZZLE_128B));
+            GPK_TRY(launch_kmvm_tc(ctx, pl, op.lay, a, op.tmA, op.tmB, op.tmV, op.outscale, op.partial, s));
+        }
+    }
+    return GP_OK;
+}
+
+}  // namespace gpk

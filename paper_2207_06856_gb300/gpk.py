@@ -1,0 +1,216 @@
+"""Thin Python binding over libgpk's C ABI (include/gpk.h).
+
+Argument marshalling only: tensors are passed as raw device pointers with the
+current torch CUDA stream; every step of the computation runs in the CUDA
+library.  There is no CPU fallback: if libgpk.so is missing, or a tensor is
+not a contiguous float32 CUDA tensor, the call raises.
+
+Layouts follow the C ABI: inputs X are (N, d) row-major; blocks of vectors are
+N x R column-major, i.e. torch tensors of shape (R, N) (row c = vector c).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgpk.so")
+
+# status codes
+GP_OK = 0
+GP_ERR_INVALID = -1
+GP_ERR_CUDA = -2
+GP_ERR_WORKSPACE = -3
+GP_ERR_BREAKDOWN = -4
+GP_ERR_NONFINITE = -5
+GP_ERR_NOT_CONVERGED = -6
+GP_ERR_TIMEOUT = -7
+GP_ERR_OOM = -8
+GP_ERR_UNSUPPORTED = -9
+
+# kernels and precisions
+RBF, MATERN32, MATERN12, MATERN52 = 0, 1, 2, 3
+KERNELS = {"rbf": RBF, "matern32": MATERN32, "matern12": MATERN12, "matern52": MATERN52}
+FP32, FP16, BF16 = 0, 1, 2
+PRECISIONS = {"fp32": FP32, "fp16": FP16, "bf16": BF16}
+
+MVM_ADD_NOISE = 0x100
+MVM_XSPLIT = 0x200
+MVM_NO_XSPLIT = 0x400
+MVM_SCALE_SQRT_N = 0x800
+MVM_VSPLIT = 0x1000
+MVM_BF16_SINGLE = 0x2000
+
+
+class GPKError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {strerror(status)} ({status})" if what else f"{strerror(status)} ({status})")
+
+
+class _Hyp(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("d", ctypes.c_int),
+                ("lengthscale", ctypes.POINTER(ctypes.c_float)),
+                ("outputscale", ctypes.c_double), ("noise", ctypes.c_double)]
+
+
+_lib = None
+_c_void_p = ctypes.c_void_p
+_c_i64 = ctypes.c_int64
+_c_int = ctypes.c_int
+_c_size = ctypes.c_size_t
+
+
+def _declare(lib):
+    sig = {
+        "gp_strerror": (ctypes.c_char_p, [_c_int]),
+        "gp_ctx_create": (_c_int, [_c_int, _c_size, ctypes.POINTER(_c_void_p)]),
+        "gp_ctx_destroy": (None, [_c_void_p]),
+        "gp_ctx_reserve": (_c_int, [_c_void_p, _c_size]),
+        "gp_ctx_workspace_bytes": (_c_size, [_c_void_p]),
+        "gp_ctx_check": (_c_int, [_c_void_p, _c_void_p]),
+        "gp_ctx_launch_count": (_c_i64, [_c_void_p]),
+        "gp_kmvm_workspace_size": (_c_size, [ctypes.POINTER(_Hyp), _c_i64, _c_i64, _c_int, _c_int]),
+        "gp_kmvm": (_c_int, [_c_void_p, ctypes.POINTER(_Hyp), _c_void_p, _c_i64, _c_void_p, _c_i64,
+                             _c_void_p, _c_int, _c_void_p, _c_int, _c_void_p]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+def lib():
+    """Load libgpk.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2207_06856_gb300.build.build()")
+        _lib = _declare(ctypes.CDLL(LIB_PATH))
+    return _lib
+
+
+def strerror(status: int) -> str:
+    return lib().gp_strerror(int(status)).decode()
+
+
+def _check(status: int, what: str):
+    if status != GP_OK:
+        raise GPKError(status, what)
+
+
+@dataclass
+class Hyper:
+    """theta = (lengthscale[d], outputscale a^2, noise sigma^2) and the kernel."""
+    kernel: int
+    lengthscale: np.ndarray
+    outputscale: float = 1.0
+    noise: float = 0.0
+
+    def __post_init__(self):
+        if isinstance(self.kernel, str):
+            self.kernel = KERNELS[self.kernel]
+        self.lengthscale = np.ascontiguousarray(np.atleast_1d(self.lengthscale), dtype=np.float32)
+
+    @property
+    def d(self) -> int:
+        return int(self.lengthscale.shape[0])
+
+    def c(self) -> _Hyp:
+        h = _Hyp(int(self.kernel), self.d,
+                 self.lengthscale.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                 float(self.outputscale), float(self.noise))
+        h._keep = self.lengthscale  # keep the array alive with the struct
+        return h
+
+
+def _stream_ptr(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _dev_ptr(t, what: str, shape=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if t.dtype != torch.float32:
+        raise TypeError(f"{what} must be float32")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{what} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return int(t.data_ptr())
+
+
+class Context:
+    """A libgpk context on one CUDA device (owns the device workspace)."""
+
+    def __init__(self, device: int = 0, workspace_bytes: int = 0):
+        self._p = _c_void_p()
+        _check(lib().gp_ctx_create(int(device), int(workspace_bytes), ctypes.byref(self._p)), "gp_ctx_create")
+        self.device = device
+
+    def close(self):
+        if self._p:
+            lib().gp_ctx_destroy(self._p)
+            self._p = _c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def ptr(self):
+        return self._p
+
+    def reserve(self, nbytes: int):
+        _check(lib().gp_ctx_reserve(self._p, int(nbytes)), "gp_ctx_reserve")
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(lib().gp_ctx_workspace_bytes(self._p))
+
+    @property
+    def launches(self) -> int:
+        return int(lib().gp_ctx_launch_count(self._p))
+
+    def check(self, stream=None):
+        _check(lib().gp_ctx_check(self._p, _c_void_p(_stream_ptr(stream))), "device error")
+
+
+def kmvm_workspace_size(hyp: Hyper, Nr: int, Nc: int, R: int, flags: int) -> int:
+    h = hyp.c()
+    return int(lib().gp_kmvm_workspace_size(ctypes.byref(h), int(Nr), int(Nc), int(R), int(flags)))
+
+
+def kmvm(ctx: Context, hyp: Hyper, Xr, V, Xc=None, precision="fp16", add_noise=False, flags=0,
+         out=None, stream=None):
+    """out = a^2 K(Xr, Xc) V (+ sigma^2 V): gp_kmvm.  Xr (Nr, d), Xc (Nc, d),
+    V (R, Nc) -> out (R, Nr), all float32 CUDA tensors."""
+    import torch
+    Xc = Xr if Xc is None else Xc
+    Nr, d = Xr.shape
+    Nc = Xc.shape[0]
+    R = V.shape[0]
+    if d != hyp.d or Xc.shape[1] != d:
+        raise ValueError("input dimension does not match the lengthscales")
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    fl = prec | int(flags) | (MVM_ADD_NOISE if add_noise else 0)
+    if out is None:
+        out = torch.empty((R, Nr), dtype=torch.float32, device=V.device)
+    need = kmvm_workspace_size(hyp, Nr, Nc, R, fl & ~MVM_ADD_NOISE)
+    if need > ctx.workspace_bytes:
+        ctx.reserve(need)
+    h = hyp.c()
+    st = lib().gp_kmvm(ctx.ptr, ctypes.byref(h), _dev_ptr(Xr, "Xr", (Nr, d)), Nr, _dev_ptr(Xc, "Xc", (Nc, d)), Nc,
+                       _dev_ptr(V, "V", (R, Nc)), R, _dev_ptr(out, "out", (R, Nr)), fl, _stream_ptr(stream))
+    _check(st, "gp_kmvm")
+    return out

@@ -1,0 +1,197 @@
+"""Parity of the CUDA kernel MVM (gp_kmvm, Eq. mvm) with the FP64 oracle.
+
+Tolerances (relative Frobenius error per right-hand side, max over columns):
+FP16 / BF16 tensor-core operands with FP32 accumulation <= 2e-3; FP32 SIMT
+<= 1e-5.  Both follow from the arithmetic: one rounding of the kernel value
+and of v to 11 (FP16) or 8 (BF16) significant bits, errors that average over
+the row sum, and FP32 accumulation (2^-24 per add)."""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2207_06856_gb300 import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "fp16": 2e-3, "bf16": 2e-3}
+KNAME = {0: "rbf", 1: "matern32", 2: "matern12", 3: "matern52"}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2207_06856_gb300 import gpk
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = gpk.Context(0)
+    yield c
+    c.close()
+
+
+def _run(ctx, X, V, kern, ls, a2, s2, prec, Xc=None, add_noise=True, flags=0, guard=64):
+    from paper_2207_06856_gb300 import gpk
+    dev = torch.device("cuda:0")
+    hyp = gpk.Hyper(kern, ls, a2, s2)
+    Xd = torch.from_numpy(X).to(dev)
+    Xcd = Xd if Xc is None else torch.from_numpy(Xc).to(dev)
+    Vd = torch.from_numpy(V).to(dev)
+    R, Nr = V.shape[0], X.shape[0]
+    buf = torch.full((R * Nr + 2 * guard,), float("nan"), device=dev)
+    out = buf[guard:guard + R * Nr].view(R, Nr)
+    gpk.kmvm(ctx, hyp, Xd, Vd, Xc=Xcd, precision=prec, add_noise=add_noise, flags=flags, out=out)
+    ctx.check()
+    b = buf.cpu().numpy()
+    assert np.all(np.isnan(b[:guard])) and np.all(np.isnan(b[-guard:])), "write outside the output"
+    return out.cpu().numpy().astype(np.float64)
+
+
+def _ref(X, V, kern, ls, a2, s2, Xc=None, add_noise=True):
+    Xc = X if Xc is None else Xc
+    return O.kmvm(X, Xc, V.T.astype(np.float64), O.Hyp(KNAME[kern], ls, a2, s2), add_noise=add_noise).T
+
+
+def _colerr(got, ref):
+    return float(np.max(np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)))
+
+
+SHAPES = [(1, 1, 1), (100, 3, 1), (129, 4, 16), (700, 8, 17), (1000, 11, 5), (333, 18, 17), (2048, 8, 17),
+          (257, 16, 33), (4097, 2, 2), (640, 30, 3)]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("kern", [0, 1, 2, 3])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_kmvm_matches_oracle(ctx, prec, kern, shape):
+    N, d, R = shape
+    X, V, _, ls, a2, s2 = workloads.random_problem(N, d, R, seed=N + d + R, kernel=kern, lengthscale=1.0,
+                                                   outputscale=1.3, noise=0.05)
+    got = _run(ctx, X, V, kern, ls, a2, s2, prec)
+    assert _colerr(got, _ref(X, V, kern, ls, a2, s2)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
+def test_kmvm_rectangular_without_noise(ctx, prec):
+    """Predictive-mean shape K(X*, X) v (Sec. 3.1): different row and column sets."""
+    X, V, kern, ls, a2, s2 = workloads.random_problem(1500, 8, 3, seed=5)
+    Xs = np.random.default_rng(6).standard_normal((300, 8)).astype(np.float32)
+    got = _run(ctx, Xs, V, kern, ls, a2, s2, prec, Xc=X, add_noise=False)
+    assert _colerr(got, _ref(Xs, V, kern, ls, a2, s2, Xc=X, add_noise=False)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("kern", [0, 1])
+def test_kmvm_rank_one_limit(ctx, prec, kern):
+    """l -> infinity: K = a^2 1 1^T, so out = a^2 (1^T v) 1 + sigma^2 v.  v has a
+    nonzero mean so 1^T v does not cancel (cancellation is covered below)."""
+    X, V, _, _, _, _ = workloads.random_problem(900, 5, 4, seed=7)
+    V = V + 1.0
+    ls = np.full(5, 1e6, np.float32)
+    got = _run(ctx, X, V, kern, ls, 1.7, 0.1, prec)
+    ref = 1.7 * np.ones((4, 900)) * V.astype(np.float64).sum(axis=1, keepdims=True) + 0.1 * V
+    assert _colerr(got, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec,flags_name", [("fp16", "vsplit"), ("bf16", "default"), ("fp32", "default")])
+def test_kmvm_rank_one_limit_with_cancellation(ctx, prec, flags_name):
+    """1^T v of 900 standard normals can be ~1 while |v| ~ 30: a single FP16
+    rounding of v then gives ~1e-2 relative error (the half-precision MVM of
+    the paper has the same property).  Carrying v as hi + lo removes it."""
+    from paper_2207_06856_gb300 import gpk
+    X, V, _, _, _, _ = workloads.random_problem(900, 5, 4, seed=7)
+    ls = np.full(5, 1e6, np.float32)
+    fl = gpk.MVM_VSPLIT if flags_name == "vsplit" else 0
+    got = _run(ctx, X, V, 0, ls, 1.7, 0.1, prec, flags=fl)
+    ref = 1.7 * np.ones((4, 900)) * V.astype(np.float64).sum(axis=1, keepdims=True) + 0.1 * V
+    assert _colerr(got, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
+def test_kmvm_far_apart_limit(ctx, prec):
+    """Points ten lengthscales apart (an 8 x 8 x 8 grid, offset far from the
+    origin): the kernel matrix is a^2 I to within exp(-50), out = (a^2 + sigma^2) v."""
+    g = np.arange(8, dtype=np.float32)
+    X = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3) + 100.0
+    N = X.shape[0]
+    V = np.random.default_rng(8).standard_normal((3, N)).astype(np.float32)
+    ls = np.full(3, 0.1, np.float32)
+    got = _run(ctx, X, V, 0, ls, 0.9, 0.2, prec)
+    assert _colerr(got, 1.1 * V.astype(np.float64)) <= TOL[prec]
+
+
+def test_kmvm_bf16_single_term(ctx):
+    """Single-term BF16 (flag): each kernel value and v rounded once to 8
+    significant bits; for random-sign v the relative error is about
+    2^-8/sqrt(3) per source, so the bound here is 8e-3, not 2e-3."""
+    from paper_2207_06856_gb300 import gpk
+    X, V, kern, ls, a2, s2 = workloads.random_problem(3000, 8, 17, seed=13)
+    got = _run(ctx, X, V, kern, ls, a2, s2, "bf16", flags=gpk.MVM_BF16_SINGLE)
+    err = _colerr(got, _ref(X, V, kern, ls, a2, s2))
+    assert err <= 8e-3
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16", "fp32"])
+def test_kmvm_symmetry(ctx, prec):
+    """u^T (Ktilde v) = v^T (Ktilde u)."""
+    X, V, kern, ls, a2, s2 = workloads.random_problem(3000, 6, 2, seed=9, kernel=1)
+    got = _run(ctx, X, V, kern, ls, a2, s2, prec)
+    u, v = V[0].astype(np.float64), V[1].astype(np.float64)
+    lhs, rhs = u @ got[1], v @ got[0]
+    assert abs(lhs - rhs) <= 4 * TOL[prec] * max(abs(lhs), np.linalg.norm(u) * np.linalg.norm(got[1]) * 1e-2)
+
+
+@pytest.mark.parametrize("flags_name", ["xsplit", "sqrtn"])
+def test_kmvm_options(ctx, flags_name):
+    from paper_2207_06856_gb300 import gpk
+    X, V, kern, ls, a2, s2 = workloads.random_problem(1200, 8, 5, seed=10)
+    fl = gpk.MVM_XSPLIT if flags_name == "xsplit" else gpk.MVM_SCALE_SQRT_N
+    got = _run(ctx, X, V, kern, ls, a2, s2, "fp16", flags=fl)
+    assert _colerr(got, _ref(X, V, kern, ls, a2, s2)) <= TOL["fp16"]
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16", "fp32"])
+def test_kmvm_precision_workload_sampled_rows(ctx, prec):
+    """The benchmark's MVM shape (N = 65,536, d = 8, 1 + 16 right-hand sides,
+    standardised Gaussian inputs, l = 1): 256 sampled rows against exact FP64 rows."""
+    w = workloads.precision()
+    from paper_2207_06856_gb300 import gpk
+    dev = torch.device("cuda:0")
+    B = w.rhs()
+    hyp = gpk.Hyper(w.kernel, w.lengthscale, w.outputscale, w.noise)
+    out = gpk.kmvm(ctx, hyp, torch.from_numpy(w.X).to(dev), torch.from_numpy(B).to(dev), precision=prec,
+                   add_noise=True)
+    ctx.check()
+    got = out.cpu().numpy().astype(np.float64)
+    rows = np.sort(np.random.default_rng(11).choice(w.N, 256, replace=False))
+    ref = O.kmvm_rows(w.X, rows, B.T.astype(np.float64), O.Hyp("rbf", w.lengthscale, w.outputscale, w.noise)).T
+    assert _colerr(got[:, rows], ref) <= TOL[prec]
+
+
+def test_kmvm_scale_workload_sampled_rows(ctx):
+    """The scale workload's MVM (N = 1,843,200, d = 11, Matern-3/2, FP16): 48 sampled rows."""
+    w = workloads.scale()
+    from paper_2207_06856_gb300 import gpk
+    dev = torch.device("cuda:0")
+    B = w.rhs()[:5]
+    hyp = gpk.Hyper(w.kernel, w.lengthscale, w.outputscale, w.noise)
+    out = gpk.kmvm(ctx, hyp, torch.from_numpy(w.X).to(dev), torch.from_numpy(B).to(dev), precision="fp16",
+                   add_noise=True)
+    ctx.check()
+    rows = np.sort(np.random.default_rng(12).choice(w.N, 48, replace=False))
+    got = out[:, torch.from_numpy(rows).to(dev)].cpu().numpy().astype(np.float64)
+    ref = O.kmvm_rows(w.X, rows, B.T.astype(np.float64), O.Hyp("matern32", w.lengthscale, w.outputscale, w.noise)).T
+    assert _colerr(got, ref) <= TOL["fp16"]
+
+
+def test_kmvm_rejects_bad_arguments(ctx):
+    from paper_2207_06856_gb300 import gpk
+    dev = torch.device("cuda:0")
+    X = torch.randn(10, 3, device=dev)
+    V = torch.randn(2, 10, device=dev)
+    with pytest.raises(gpk.GPKError):
+        gpk.kmvm(ctx, gpk.Hyper(0, np.array([1.0, -1.0, 1.0]), 1.0, 0.1), X, V)
+    with pytest.raises(gpk.GPKError):
+        gpk.kmvm(ctx, gpk.Hyper(0, np.ones(3), 1.0, 0.1), X, V, Xc=torch.randn(12, 3, device=dev)[:10],
+                 add_noise=True)
+    with pytest.raises(gpk.GPKError):
+        gpk.kmvm(ctx, gpk.Hyper(0, np.ones(3), 1.0, 0.1), X, torch.randn(65, 10, device=dev))
