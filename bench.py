@@ -1,0 +1,385 @@
+"""Benchmark: time to CG relative residual 1e-2 on the precision workload.
+
+Workload (one "step"): N = 65,536 standardised Gaussian points in d = 8, RBF
+kernel (l = 1, a^2 = 1, sigma^2 = 0.05), B = [y, 16 Rademacher probes]
+(17 right-hand sides), rank-100 pivoted-Cholesky preconditioner, then the
+stable CG (Alg. 2) with FP16 tensor-core MVMs until every column's
+relative residual, recomputed with an FP32 MVM, is <= 1e-2.  The step is the
+whole hot path: operand preparation, preconditioner factor + core, every MVM,
+Woodbury apply, LSE scalars, re-orthogonalisation, residual checks.
+
+Printed: one JSON line (rank 0).  `value` = seconds per solve (lower is
+better), device-timed with CUDA events, inputs resident in HBM, L2 flushed
+between steps.  `e2e` = the same through the public API with pinned host
+buffers (X, B uploaded and U downloaded inside the timed region).  The FP32
+comparator (plain Alg. 1, SIMT FP32 MVM) and the BF16 arm are timed on the
+same inputs and reported under "arms".
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (rows of the matrix-free MVM) and extrapolates to a full solve.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time_to_cg_relresid_1e-2"
+UNIT = "s"
+TOL = 1e-2
+MAX_ITER = 1000
+FP32_ITERS_NOTE = "iterations of the FP32 stable CG on this workload"
+
+
+def _peaks_file():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        smax = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if "Active" in r[4 + i]
+                          and "Not" not in r[4 + i]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def _rank_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+# ---------------------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------------------
+
+def run_reference(args):
+    rank, world, _ = _rank_env()
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2207_06856_gb300 import workloads
+    w = workloads.precision()
+    B = w.rhs().T.astype(np.float64)
+    hyp = O.Hyp("rbf", w.lengthscale, w.outputscale, w.noise)
+    rows_per_step = 512
+    rng = np.random.default_rng(0)
+    fp32_iters = args.ref_iters
+
+    def step():
+        rows = np.sort(rng.choice(w.N, rows_per_step, replace=False))
+        t0 = time.perf_counter()
+        O.kmvm_rows(w.X, rows, B, hyp)
+        return time.perf_counter() - t0
+
+    for _ in range(args.warmup):
+        step()
+    ts = [step() for _ in range(args.steps)]
+    t_rows = float(np.mean(ts))
+    # one CG iteration = one full MVM (N rows) + O(N R) vector work (neglected)
+    per_iter = t_rows * (w.N / rows_per_step)
+    value = per_iter * fp32_iters
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_rows, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "precision: N=65536 d=8 RBF l=1 sigma2=0.05, 1+16 RHS, rank-100 pivoted Cholesky",
+                   "global_batch": 17, "seq_len": 65536, "parallelism": "none (host cores)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"FP64 matrix-free MVM of {rows_per_step} random rows x 65536 columns x 17 RHS "
+                                   f"per step, extrapolated x{w.N // rows_per_step} rows x {fp32_iters} "
+                                   f"iterations ({FP32_ITERS_NOTE})"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    rank, world, local_rank = _rank_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+
+    from paper_2207_06856_gb300 import gpk, workloads
+    w = workloads.precision(kernel=gpk.KERNELS[args.kernel])
+    hyp = gpk.Hyper(w.kernel, w.lengthscale, w.outputscale, w.noise)
+    ctx = gpk.Context(local_rank)
+    Xh = torch.from_numpy(w.X).pin_memory()
+    Bh = torch.from_numpy(w.rhs()).pin_memory()
+    X = Xh.to(dev)
+    B = Bh.to(dev)
+    R, N = B.shape
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def solve(prec, alg, reorth, Xd, Bd, Uout=None):
+        pc = gpk.pivchol(ctx, hyp, Xd, w.rank)
+        U, st, info = gpk.cg_solve(ctx, hyp, Xd, Bd, pc, tol=TOL, max_iter=MAX_ITER, precision=prec,
+                                   algorithm=alg, reorth=reorth, U=None)
+        if st != gpk.GP_OK:
+            raise RuntimeError(f"solve did not converge: status {st}, residuals {info['rel_resid']}")
+        return U, info
+
+    def timed(prec, alg, reorth, steps, warmup):
+        for _ in range(warmup):
+            solve(prec, alg, reorth, X, B)
+        torch.cuda.synchronize()
+        times, infos = [], []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            U, info = solve(prec, alg, reorth, X, B)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            infos.append(info)
+        return times, infos, U
+
+    # --- headline arm: FP16 stable CG --------------------------------------------------
+    ctx.profile(False)
+    sampler = ClockSampler(local_rank)
+    launches0 = ctx.launches
+    ctx.profile(True)
+    sampler.start()
+    times, infos, U = timed(args.precision, "stable", "pinv", args.steps, args.warmup)
+    clocks = sampler.stop()
+    prof_ms, prof_n = ctx.profile_read()
+    ctx.profile(False)
+    gpu_launches = ctx.launches - launches0
+    # launches inside the timed steps only (warm-up solves launch the same number)
+    gpu_launches = int(round(gpu_launches * args.steps / (args.steps + args.warmup)))
+    t_step = float(np.mean(times))
+    if world > 1:
+        t = torch.tensor([t_step], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(t.item())
+
+    # --- residual recomputed in FP64 on sampled rows (verification, untimed) -------------
+    resid = None
+    if rank == 0 and not args.skip_verify:
+        import oracle as O
+        rows = np.sort(np.random.default_rng(1).choice(N, 1024, replace=False))
+        oh = O.Hyp(workloads.KERNEL_NAMES[w.kernel], w.lengthscale, w.outputscale, w.noise)
+        resid = O.relative_residual(w.X, U.cpu().numpy().T, w.rhs().T, oh, rows=rows)
+
+    # --- roofline of the dominant kernel (tensor-core MVM) ------------------------------
+    pairs_per_launch = float(N) * float(N)
+    avg_launch_s = (prof_ms / 1e3 / prof_n) if prof_n else float("nan")
+    achieved = pairs_per_launch / avg_launch_s / 1e9       # Gpairs/s
+    peaks = ctx.measure_peaks()
+    mufu_per_pair = 1 if w.kernel == gpk.RBF else 2
+    peak_meas = peaks["ex2_per_s"] / mufu_per_pair / 1e9 if w.kernel == gpk.RBF else \
+        1.0 / (1.0 / peaks["ex2_per_s"] + 1.0 / peaks["sqrt_per_s"]) / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_meas, "unit": "Gpairs/s",
+                "frac": achieved / peak_meas, "traffic": None,
+                "kernel": "kmvm_tc_kernel (FP16 tensor-core kernel MVM)",
+                "peak_source": "measured special-function-unit ex2 rate on this GPU (gp_measure_peaks), "
+                               f"{mufu_per_pair} SFU op(s) per kernel pair",
+                "units_per_launch": pairs_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
+                "launches_timed": prof_n, "measured_unit_peaks": peaks}
+
+    # --- comparison arms (same inputs, same preconditioner) ------------------------------
+    arms = {}
+    if not args.no_arms:
+        for name, prec, alg, ro in [("fp32_plain_alg1", "fp32", "standard", "none"),
+                                    ("bf16_stable_alg2", "bf16", "stable", "pinv"),
+                                    ("fp32_stable_alg2", "fp32", "stable", "pinv")]:
+            ts, inf, _ = timed(prec, alg, ro, max(1, min(args.steps, 2)), 1)
+            arms[name] = {"s_per_solve": float(np.mean(ts)), "iters": int(inf[-1]["iters"]),
+                          "restarts": int(inf[-1]["restarts"])}
+
+    # --- end to end through the public API with host buffers ----------------------------
+    e2e_times = []
+    Uh = torch.empty((R, N), dtype=torch.float32).pin_memory()
+    for i in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Xd = Xh.to(dev, non_blocking=True)
+        Bd = Bh.to(dev, non_blocking=True)
+        Ud, _ = solve(args.precision, "stable", "pinv", Xd, Bd)
+        Uh.copy_(Ud, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_times.append(e0.elapsed_time(e1) / 1e3)
+    h2d = Xh.numel() * 4 + Bh.numel() * 4
+    d2h = Uh.numel() * 4
+
+    # --- CPU baseline: the FP64 oracle on a bounded sample (rank 0, N = 1 only) ----------
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        import oracle as O
+        oh = O.Hyp(workloads.KERNEL_NAMES[w.kernel], w.lengthscale, w.outputscale, w.noise)
+        Bt = w.rhs().T.astype(np.float64)
+        rows = np.sort(np.random.default_rng(2).choice(N, 512, replace=False))
+        O.kmvm_rows(w.X, rows[:64], Bt, oh)
+        t0 = time.perf_counter()
+        reps = 0
+        while time.perf_counter() - t0 < args.cpu_seconds:
+            O.kmvm_rows(w.X, rows, Bt, oh)
+            reps += 1
+        t_rows = (time.perf_counter() - t0) / reps
+        iters = arms.get("fp32_stable_alg2", {}).get("iters", infos[-1]["iters"])
+        cpu_val = t_rows * (N / len(rows)) * iters
+        cpu = {"value": cpu_val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"FP64 matrix-free MVM, {len(rows)} random rows x {N} columns x {R} RHS, "
+                         f"{reps} reps in {args.cpu_seconds:.0f}s, extrapolated to {N} rows x {iters} CG iterations"}
+
+    if rank == 0:
+        inf = infos[-1]
+        line = {
+            "metric": METRIC, "value": t_step, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": f"precision: N={N} d=8 {args.kernel} l=1 a2=1 sigma2=0.05, 1+16 RHS "
+                                   f"(y + Rademacher), rank-100 pivoted Cholesky, stable CG (Alg. 2) to "
+                                   f"rel. resid 1e-2 with FP32 residual checks",
+                       "global_batch": R, "seq_len": N, "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "flushed between steps (256 MB write)"},
+            "iters": int(inf["iters"]), "restarts": int(inf["restarts"]),
+            "final_rel_resid_max": float(np.max(inf["rel_resid"])),
+            "fp64_rel_resid_sampled_max": None if resid is None else float(np.max(resid)),
+            "kmvm_pairs_per_s": achieved * 1e9,
+            "arms": arms,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": float(np.mean(e2e_times)), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": gpu_launches,
+            "clocks": clocks,
+            "peaks_file": {k: _peaks_file().get(k) for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained")},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def run_kmvm(args):
+    """MVM launches only, at the workload's shape (N = 65,536, 17 RHS): used for
+    kernel-level ncu captures with a small device footprint."""
+    import torch
+    from paper_2207_06856_gb300 import gpk, workloads
+    w = workloads.precision(kernel=gpk.KERNELS[args.kernel])
+    hyp = gpk.Hyper(w.kernel, w.lengthscale, w.outputscale, w.noise)
+    ctx = gpk.Context(0)
+    X = torch.from_numpy(w.X).cuda()
+    B = torch.from_numpy(w.rhs()).cuda()
+    out = torch.empty_like(B)
+    for _ in range(args.warmup):
+        gpk.kmvm(ctx, hyp, X, B, precision=args.precision, add_noise=True, out=out)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        gpk.kmvm(ctx, hyp, X, B, precision=args.precision, add_noise=True, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms, n = ctx.profile_read()
+    if n == 0:   # the SIMT engine is not event-profiled: time the whole calls
+        ms, n = e0.elapsed_time(e1), args.steps
+    ctx.check()
+    pairs = float(w.N) ** 2
+    print(json.dumps({"mode": "kmvm", "precision": args.precision, "kernel": args.kernel, "launches": n,
+                      "avg_launch_ms": ms / max(n, 1), "pairs_per_s": pairs / (ms / max(n, 1) / 1e3)}), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp16", choices=["fp16", "bf16", "fp32"])
+    ap.add_argument("--kernel", default="rbf", choices=["rbf", "matern32"])
+    ap.add_argument("--no-arms", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-verify", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-iters", type=int, default=152)
+    ap.add_argument("--mode", default="solve", choices=["solve", "kmvm"])
+    args = ap.parse_args()
+    if args.mode == "kmvm":
+        run_kmvm(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -113,6 +113,21 @@ GPK_API int64_t gp_ctx_launch_count(const gp_ctx* ctx);
 /* Static description of a status code. */
 GPK_API const char* gp_strerror(int status);
 
+/* ---- measurement support (Sec. 4.1 timing study) --------------------------
+ * gp_ctx_profile(ctx, 1) records a CUDA event pair around every tensor-core
+ * MVM launch on its stream (up to 8192 launches; creates the events, so call
+ * it outside timed regions).  gp_ctx_profile_read synchronises those events,
+ * returns the summed launch time in ms and the launch count, and resets.
+ * gp_measure_peaks runs throughput loops (8 independent chains per thread,
+ * 8 CTAs of 256 threads per SM) and returns the best of 5 rates in
+ * operations/s for ex2.approx.f32 and sqrt.approx.f32 (special function
+ * units) and FP32 FMA; it allocates 256 B of scratch.  Diagnostic only: the
+ * paper has no counterpart. */
+GPK_API int gp_ctx_profile(gp_ctx* ctx, int enable);
+GPK_API int gp_ctx_profile_read(gp_ctx* ctx, double* total_ms, int64_t* launches);
+GPK_API int gp_measure_peaks(gp_ctx* ctx, double* ex2_per_s, double* sqrt_per_s, double* ffma_per_s,
+                             void* stream);
+
 /* ---- S1+S2: matrix-free kernel MVM (Eq. mvm, Sec. 4.1) --------------------
  *   out[:, c] = a^2 K(Xr, Xc) V[:, c]  (+ sigma^2 V[:, c] with GP_MVM_ADD_NOISE)
  * K is never stored: 128 x 128 tiles of the kernel matrix are formed on chip
@@ -129,6 +144,94 @@ GPK_API size_t gp_kmvm_workspace_size(const gp_hyp_t* hyp, int64_t Nr, int64_t N
 GPK_API int gp_kmvm(gp_ctx* ctx, const gp_hyp_t* hyp,
             const float* Xr, int64_t Nr, const float* Xc, int64_t Nc,
             const float* V, int R, float* out, int flags, void* stream);
+
+/* ---- S3: pivoted-Cholesky preconditioner (Sec. 4.2, Eq. woodbury) ---------
+ * k = rank steps of partial pivoted Cholesky of K (no noise) from kernel rows
+ * K e_p and the constant diagonal a^2: pivot = argmax of the remaining
+ * diagonal (lowest index on ties); stops early when that value falls to
+ * 1e-6 a^2 (FP32 rows).  Then the Woodbury core C = I + sigma^-2 L^T L is
+ * formed and factored in FP64.  P = L L^T + sigma^2 I.
+ *   X     device, N x d row-major FP32
+ *   L     device, N x rank column-major FP32 (columns >= rank_out undefined)
+ *   piv   device, int32 [rank] pivot indices
+ *   core  device, rank_out x rank_out column-major FP64, lower factor Lc of C
+ *         (C = Lc Lc^T; leading dimension rank_out)
+ *   rank_out host: the rank reached.  Synchronises the stream.
+ * Requires 1 <= rank <= min(N, 512) and noise > 0. */
+GPK_API size_t gp_pivchol_workspace_size(const gp_hyp_t* hyp, int64_t N, int rank);
+GPK_API int gp_pivchol_precond(gp_ctx* ctx, const gp_hyp_t* hyp, const float* X, int64_t N, int rank,
+                               float* L, int32_t* piv, double* core, int* rank_out, void* stream);
+
+/* Preconditioner handed to the solvers: P^{-1} w = sigma^-2 w -
+ * sigma^-4 L C^{-1} L^T w (Eq. woodbury).  rank = 0 means no preconditioner
+ * (P = I). */
+typedef struct {
+    const float* L;       /* device, N x rank column-major FP32               */
+    const double* core;   /* device, rank x rank lower Cholesky factor of C   */
+    int rank;
+} gp_precond_t;
+
+/* ---- S4-S6: preconditioned conjugate gradients (Alg. 1, Alg. 2, App. A) ---- */
+#define GP_CG_STABLE     0  /* Alg. 2: log-scale alpha/beta (LSE), re-orthogonalisation */
+#define GP_CG_STANDARD   1  /* Alg. 1: textbook preconditioned CG                          */
+#define GP_REORTH_NONE   0
+#define GP_REORTH_PINV   1  /* project against past residuals in the P^{-1} inner product,
+                               in which preconditioned residuals are orthogonal (default) */
+#define GP_REORTH_EUCLID 2  /* literal Alg. 2: Euclidean-normalised past residuals
+                               (exactly orthogonal only when P = I)                       */
+
+typedef struct {
+    double tol;          /* stop column c when ||r_c|| / ||b_c|| <= tol (recursive residual) */
+    int max_iter;        /* 1 .. 1000                                                       */
+    int min_iter;        /* iterations run before the tolerance is tested                   */
+    int precision;       /* MVM flags: GP_PREC_* | GP_MVM_* option bits (no ADD_NOISE)      */
+    int algorithm;       /* GP_CG_STABLE or GP_CG_STANDARD                                  */
+    int reorth;          /* GP_REORTH_*; only used by GP_CG_STABLE                          */
+    int reorth_passes;   /* 1 = classical Gram-Schmidt, 2 = twice (CGS2)                    */
+    int x0_given;        /* nonzero: U holds the initial guess x_0 on entry                 */
+    int restarts;        /* true-residual checks: when every column has met tol on its
+                            recursive residual, r = K x - b is recomputed with the same
+                            MVM and columns still above tol restart from their current x
+                            (fresh basis); at most this many times.  0 = trust the
+                            recursive residual (re-orthogonalisation changes r but not
+                            x, so the two drift apart by rounding)                   */
+    int check_precision; /* GP_PREC_* of the MVM that recomputes r = K x - b at a
+                            true-residual check.  GP_PREC_FP32 turns the restarts into
+                            mixed-precision iterative refinement: a half-precision MVM
+                            cannot resolve the residual of its own solution when
+                            K x cancels heavily (|x| >> |b| for small sigma^2)       */
+} gp_cg_opts_t;
+
+/* Host-side statistics (every pointer may be NULL). */
+typedef struct {
+    int iters;           /* iterations run (max over columns)                 */
+    int converged;       /* columns that reached tol                          */
+    int breakdowns;      /* columns stopped by an LSE breakdown               */
+    int restarts;        /* true-residual restarts performed                  */
+    int* col_iters;      /* [R]                                               */
+    double* rel_resid;   /* [R] final relative residual: the recomputed one after a
+                            true-residual check, else the recursive one           */
+    double* alpha;       /* [max_iter * R]: alpha_k of column c at k*R + c    */
+    double* beta;        /* [max_iter * R]: beta_{k+1} of column c at k*R + c */
+    double* gamma0;      /* [R] r_0^T z_0                                     */
+    double* resid_hist;  /* [(max_iter + 1) * R] relative residual per iterate */
+} gp_cg_stats_t;
+
+/* Solve (K + sigma^2 I) U = B for R right-hand sides at once (Eq. cg; mBCG of
+ * App. A: every column has its own alpha_k, beta_k and stops on its own).
+ * The MVM inside is gp_kmvm's (precision from opts).  Scalars alpha, beta,
+ * gamma, the residual norms and the re-orthogonalisation coefficients are
+ * FP64; vectors are FP32.
+ *   X  device N x d; B device N x R column-major; U device N x R (in: x_0 when
+ *   opts->x0_given, out: solution).  1 <= R <= 64.
+ * Synchronises the stream once per iteration (convergence flags).
+ * Returns GP_OK when every column converged, GP_ERR_NOT_CONVERGED when some
+ * did not within max_iter (U and stats still valid), GP_ERR_BREAKDOWN when a
+ * column's LSE sum was not positive (that column keeps its last iterate). */
+GPK_API size_t gp_cg_workspace_size(const gp_hyp_t* hyp, int64_t N, int R, int rank, const gp_cg_opts_t* opts);
+GPK_API int gp_cg_solve(gp_ctx* ctx, const gp_hyp_t* hyp, const float* X, int64_t N, const float* B, int R,
+                        float* U, const gp_precond_t* precond, const gp_cg_opts_t* opts, gp_cg_stats_t* stats,
+                        void* stream);
 
 #ifdef __cplusplus
 }

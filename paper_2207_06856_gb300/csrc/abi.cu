@@ -98,6 +98,8 @@ void gp_ctx_destroy(gp_ctx* ctx) {
     cudaDeviceSynchronize();
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->dev_err) cudaFree(ctx->dev_err);
+    if (ctx->prof_ev_ready)
+        for (int i = 0; i < 2 * gpk::Ctx::kProfMax; ++i) cudaEventDestroy(ctx->prof_ev[i]);
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
     delete ctx;
 }

@@ -1,0 +1,608 @@
+// S5 + S6: enhanced-stability preconditioned CG (Alg. 2) and textbook
+// preconditioned CG (Alg. 1), for R right-hand sides at once with per-column
+// scalars (mBCG, App. A).
+//
+// Alg. 2 as run here (r = K x - b sign convention of the paper):
+//   r_0 = K(x_0) - b,  z_0 = P^{-1} r_0,  d_0 = -z_0,  log gamma_0 = LSE(r_0^T z_0)
+//   repeat:  log alpha = log gamma - LSE(d^T K d);  x += alpha d;  r += alpha K d
+//            r <- r - sum_j (zeta_j^T r) rho_j        (re-orthogonalisation)
+//            z = P^{-1} r;  log gamma' = LSE(r^T z);  beta = exp(log gamma' - log gamma)
+//            d = -z + beta d
+// The loop condition is read as "relative residual above tol" (the printed
+// condition is inverted), d is formed from z (the printed -r is the P = I
+// case), and P(.) applies P^{-1} (Eq. woodbury).
+//
+// LSE.  The paper's transformation log w^T z = y_max + log sum s_i
+// exp(y_i - y_max), y_i = log|w_i| + log|z_i|, holds for any shift.  The GPU
+// takes the shift as a power of two: each FP32 x FP32 product is exact in
+// FP64, every thread keeps (e, s) with |p| 2^-e < 1 and s = sum p 2^-e,
+// partial pairs are merged in a fixed order, and LSE = log(s) + e log 2.  No
+// per-element transcendental is needed and nothing can overflow or
+// underflow.  A non-positive s is a breakdown of that column.
+//
+// Re-orthogonalisation.  In PCG the residuals are mutually orthogonal in the
+// P^{-1} inner product, so the default stores rho_j = r_j / sqrt(gamma_j),
+// zeta_j = z_j / sqrt(gamma_j) and projects r <- r - sum_j (zeta_j^T r) rho_j
+// (classical Gram-Schmidt, optionally twice; coefficients accumulated in
+// FP64).  GP_REORTH_EUCLID stores u_j = r_j / ||r_j|| (the literal form).
+//
+// The only host/device round trip per iteration is a 4-byte copy of the
+// number of still-active columns.
+#include "gpk_internal.cuh"
+
+#include <math.h>
+#include <string.h>
+
+namespace gpk {
+
+namespace {
+
+constexpr int kDotThreads = 256;
+constexpr int kDotPerThread = 8;
+constexpr int kDotChunk = kDotThreads * kDotPerThread;
+constexpr int kEmptyExp = -100000;
+
+struct ColState {
+    double log_gamma;   // log r^T z (both algorithms keep it; Alg. 1 also keeps gamma)
+    double gamma;
+    double alpha, beta;
+    double bnorm, rnorm, relres;
+    double gamma0;      // r_0^T z_0 (the SLQ quadrature weight ||P^{-1/2} r_0||^2)
+    int active;
+    int iters;
+    int breakdown;
+    int pad;
+};
+
+struct Lse {
+    double s;
+    int e;
+};
+
+__device__ __forceinline__ void lse_add(Lse& a, double p) {
+    if (p == 0.0) return;
+    int ep;
+    frexp(p, &ep);   // |p| < 2^ep
+    if (ep > a.e) {
+        a.s = (a.e == kEmptyExp) ? 0.0 : ldexp(a.s, a.e - ep);
+        a.e = ep;
+    }
+    a.s += ldexp(p, -a.e);
+}
+
+__device__ __forceinline__ void lse_merge(Lse& a, const Lse& b) {
+    if (b.e == kEmptyExp) return;
+    if (a.e == kEmptyExp) { a = b; return; }
+    if (b.e > a.e) {
+        a.s = ldexp(a.s, a.e - b.e) + b.s;
+        a.e = b.e;
+    } else {
+        a.s += ldexp(b.s, b.e - a.e);
+    }
+}
+
+__device__ __forceinline__ Lse lse_shfl(const Lse& a, int o) {
+    Lse b;
+    b.s = __shfl_xor_sync(0xffffffffu, a.s, o);
+    b.e = __shfl_xor_sync(0xffffffffu, a.e, o);
+    return b;
+}
+
+// part[(c * nblk + blk) * 3 + {0,1,2}] = (s, e, sum a^2) of column c over this chunk.
+__global__ void __launch_bounds__(kDotThreads)
+dots_kernel(const float* __restrict__ A, const float* __restrict__ B, int64_t N, int nblk,
+            const int* __restrict__ active, double* __restrict__ part) {
+    const int c = blockIdx.y;
+    if (active && !active[c]) return;
+    const float* a = A + (int64_t)c * N;
+    const float* b = B + (int64_t)c * N;
+    Lse acc{0.0, kEmptyExp};
+    double n2 = 0.0;
+    const int64_t base = (int64_t)blockIdx.x * kDotChunk;
+#pragma unroll
+    for (int q = 0; q < kDotPerThread; ++q) {
+        const int64_t i = base + q * kDotThreads + threadIdx.x;
+        if (i < N) {
+            const double av = a[i], bv = b[i];
+            lse_add(acc, av * bv);
+            n2 = fma(av, av, n2);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lse_merge(acc, lse_shfl(acc, o));
+        n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+    }
+    __shared__ double ss[kDotThreads / 32], sn[kDotThreads / 32];
+    __shared__ int se[kDotThreads / 32];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { ss[w] = acc.s; se[w] = acc.e; sn[w] = n2; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Lse t{ss[0], se[0]};
+        double tn = sn[0];
+        for (int q = 1; q < kDotThreads / 32; ++q) {
+            lse_merge(t, Lse{ss[q], se[q]});
+            tn += sn[q];
+        }
+        double* o = part + ((int64_t)c * nblk + blockIdx.x) * 3;
+        o[0] = t.s;
+        o[1] = (double)t.e;
+        o[2] = tn;
+    }
+}
+
+enum ScalarMode { SC_INIT = 0, SC_ALPHA = 1, SC_BETA = 2, SC_BNORM = 3 };
+
+// One block, one warp per column: merge the partials of column c in a fixed
+// order, then run the scalar step of Alg. 1 / Alg. 2.
+__global__ void scalar_kernel(int mode, int stable, const double* __restrict__ part, int nblk, int R,
+                              ColState* __restrict__ st, int k, double tol, int min_iter, double* __restrict__ ahist,
+                              double* __restrict__ bhist, double* __restrict__ rhist, int* __restrict__ n_active) {
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int c = w; c < R; c += (blockDim.x >> 5)) {
+        ColState& S = st[c];
+        const bool act = (mode == SC_INIT || mode == SC_BNORM) ? true : (S.active != 0);
+        if (act) {
+            Lse acc{0.0, kEmptyExp};
+            double n2 = 0.0;
+            for (int b = l; b < nblk; b += 32) {
+                const double* o = part + ((int64_t)c * nblk + b) * 3;
+                lse_merge(acc, Lse{o[0], (int)o[1]});
+                n2 += o[2];
+            }
+            // fixed-order tree merge across lanes
+            for (int off = 16; off > 0; off >>= 1) {
+                lse_merge(acc, lse_shfl(acc, off));
+                n2 += __shfl_xor_sync(0xffffffffu, n2, off);
+            }
+            if (l == 0) {
+                const bool pos = acc.e != kEmptyExp && acc.s > 0.0;
+                const double lse = pos ? log(acc.s) + (double)acc.e * 0.6931471805599453 : -INFINITY;
+                const double val = pos ? ldexp(acc.s, acc.e) : 0.0;
+                if (mode == SC_BNORM) {
+                    S.bnorm = sqrt(n2);
+                } else if (mode == SC_INIT) {
+                    S.rnorm = sqrt(n2);
+                    S.relres = S.bnorm > 0.0 ? S.rnorm / S.bnorm : 0.0;
+                    S.log_gamma = lse;
+                    S.gamma = val;
+                    S.gamma0 = val;
+                    S.alpha = 0.0;
+                    S.beta = 0.0;
+                    S.iters = k;
+                    S.breakdown = 0;
+                    const bool work = S.bnorm > 0.0 && S.rnorm > 0.0 && (S.relres > tol || min_iter > k);
+                    if (work && !pos) S.breakdown = 1;
+                    S.active = (work && pos) ? 1 : 0;
+                    if (rhist) rhist[(int64_t)k * R + c] = S.relres;
+                } else if (mode == SC_ALPHA) {
+                    // alpha_k = gamma_k / d^T K d  (Alg. 2: in log scale)
+                    if (!pos) {
+                        S.breakdown = 1;
+                        S.active = 0;
+                        S.alpha = 0.0;
+                    } else {
+                        S.alpha = stable ? exp(S.log_gamma - lse) : S.gamma / val;
+                    }
+                    if (ahist) ahist[(int64_t)k * R + c] = S.alpha;
+                } else {   // SC_BETA
+                    S.rnorm = sqrt(n2);
+                    S.relres = S.bnorm > 0.0 ? S.rnorm / S.bnorm : 0.0;
+                    S.iters = k + 1;
+                    if (rhist) rhist[(int64_t)(k + 1) * R + c] = S.relres;
+                    if (S.rnorm == 0.0) {
+                        S.active = 0;           // exact solution reached
+                        S.beta = 0.0;
+                    } else if (!pos) {
+                        S.breakdown = 1;
+                        S.active = 0;
+                        S.beta = 0.0;
+                    } else {
+                        S.beta = stable ? exp(lse - S.log_gamma) : val / S.gamma;
+                        S.log_gamma = lse;
+                        S.gamma = val;
+                        if (bhist) bhist[(int64_t)k * R + c] = S.beta;
+                        if (S.relres <= tol && k + 1 >= min_iter) S.active = 0;
+                    }
+                }
+                if (S.active) atomicAdd(&cnt, 1);
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && n_active) *n_active = cnt;
+}
+
+// x += alpha d; r += alpha Kd   (active columns)
+__global__ void update_xr_kernel(float* __restrict__ x, float* __restrict__ r, const float* __restrict__ d,
+                                 const float* __restrict__ Kd, int64_t N, const ColState* __restrict__ st) {
+    const int c = blockIdx.y;
+    if (!st[c].active) return;
+    const float a = (float)st[c].alpha;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = (int64_t)c * N + i;
+        x[o] = fmaf(a, d[o], x[o]);
+        r[o] = fmaf(a, Kd[o], r[o]);
+    }
+}
+
+// r = s * src - b ; x = 0 (x0 not given) or r = Kx0 - b
+__global__ void init_r_kernel(float* __restrict__ r, const float* __restrict__ Kx, const float* __restrict__ b,
+                              float* __restrict__ x, int64_t total, int zero_x) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        r[i] = (Kx ? Kx[i] : 0.0f) - b[i];
+        if (zero_x) x[i] = 0.0f;
+    }
+}
+
+__global__ void copy_active_kernel(float* __restrict__ dst, const float* __restrict__ src, int64_t N,
+                                   const ColState* __restrict__ st) {
+    const int c = blockIdx.y;
+    if (st && !st[c].active) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        dst[(int64_t)c * N + i] = src[(int64_t)c * N + i];
+}
+
+// d = -z + beta d (beta = 0 at the start), then store the basis vectors of
+// this iterate: pinv: rho = r / sqrt(gamma), zeta = z / sqrt(gamma); euclid:
+// u = r / ||r||.
+__global__ void update_d_kernel(float* __restrict__ d, const float* __restrict__ z, const float* __restrict__ r,
+                                int64_t N, const ColState* __restrict__ st, int first, int reorth,
+                                float* __restrict__ rho, float* __restrict__ zeta) {
+    const int c = blockIdx.y;
+    const ColState& S = st[c];
+    if (!S.active) return;
+    const float beta = first ? 0.0f : (float)S.beta;
+    const float sg = (reorth == GP_REORTH_PINV) ? (float)(1.0 / sqrt(S.gamma))
+                                                : (float)(S.rnorm > 0.0 ? 1.0 / S.rnorm : 0.0);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = (int64_t)c * N + i;
+        const float zi = z[o];
+        d[o] = first ? -zi : fmaf(beta, d[o], -zi);
+        if (reorth != GP_REORTH_NONE) {
+            rho[o] = r[o] * sg;
+            if (reorth == GP_REORTH_PINV) zeta[o] = zi * sg;
+        }
+    }
+}
+
+// gpart[(c * nblk + blk) * nb + j] = sum over the chunk of ZB_j[c][i] r[c][i]
+// (FP32 products summed per thread over its 8 elements, FP64 across threads).
+__global__ void __launch_bounds__(kDotThreads)
+gram_kernel(const float* __restrict__ ZB, int nb, int R, const float* __restrict__ r, int64_t N, int nblk,
+            const ColState* __restrict__ st, double* __restrict__ gpart) {
+    const int c = blockIdx.y;
+    if (!st[c].active) return;
+    const int64_t base = (int64_t)blockIdx.x * kDotChunk;
+    float rv[kDotPerThread];
+#pragma unroll
+    for (int q = 0; q < kDotPerThread; ++q) {
+        const int64_t i = base + q * kDotThreads + threadIdx.x;
+        rv[q] = i < N ? r[(int64_t)c * N + i] : 0.0f;
+    }
+    __shared__ double sred[kDotThreads / 32];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int j = 0; j < nb; ++j) {
+        const float* zb = ZB + ((int64_t)j * R + c) * N;
+        float a = 0.0f;
+#pragma unroll
+        for (int q = 0; q < kDotPerThread; ++q) {
+            const int64_t i = base + q * kDotThreads + threadIdx.x;
+            if (i < N) a = fmaf(zb[i], rv[q], a);
+        }
+        double v = a;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (l == 0) sred[w] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < kDotThreads / 32; ++q) t += sred[q];
+            gpart[((int64_t)c * nblk + blockIdx.x) * nb + j] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// coef[j * R + c] = sum_blk gpart  (fixed order)
+__global__ void gram_finalize_kernel(const double* __restrict__ gpart, int nblk, int nb, int R,
+                                     const ColState* __restrict__ st, double* __restrict__ coef) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nb * R) return;
+    const int j = e / R, c = e % R;
+    if (!st[c].active) return;
+    double t = 0.0;
+    for (int b = 0; b < nblk; ++b) t += gpart[((int64_t)c * nblk + b) * nb + j];
+    coef[e] = t;
+}
+
+// r -= sum_j coef[j][c] RB_j[c]
+__global__ void reorth_update_kernel(const float* __restrict__ RB, int nb, int R, const double* __restrict__ coef,
+                                     float* __restrict__ r, int64_t N, const ColState* __restrict__ st) {
+    const int c = blockIdx.y;
+    if (!st[c].active) return;
+    __shared__ float sc[1024];
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) sc[j] = (float)coef[j * R + c];
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        float v = r[(int64_t)c * N + i];
+        for (int j = 0; j < nb; ++j) v = fmaf(-sc[j], RB[((int64_t)j * R + c) * N + i], v);
+        r[(int64_t)c * N + i] = v;
+    }
+}
+
+// The active flags of the Woodbury kernels, as a plain int array.
+__global__ void active_flags_kernel(const ColState* __restrict__ st, int R, int* __restrict__ flags) {
+    const int c = threadIdx.x;
+    if (c < R) flags[c] = st[c].active;
+}
+
+struct CgBufs {
+    float *r, *z, *d, *Kd, *rho, *zeta;
+    double *dpart, *gpart, *coef, *ahist, *bhist, *rhist;
+    ColState* st;
+    int* nact;
+    int* aflags;
+    int nb_max, nblk_dot;
+};
+
+int vec_grid(const Ctx* ctx, int64_t N) {
+    int64_t g = (N + 255) / 256;
+    const int64_t cap = 2 * (int64_t)(ctx->num_sms > 0 ? ctx->num_sms : 148);
+    return (int)(g < cap ? g : cap);
+}
+
+template <class A>
+void cg_layout(A& a, const Ctx* ctx, int64_t N, int R, int rank, const gp_cg_opts_t* o) {
+    const size_t NR = (size_t)N * R;
+    a.template take<float>(NR);   // r
+    a.template take<float>(NR);   // z
+    a.template take<float>(NR);   // d
+    a.template take<float>(NR);   // Kd
+    const bool re = o->algorithm == GP_CG_STABLE && o->reorth != GP_REORTH_NONE;
+    const int nb_max = o->max_iter + 1;   // a restart starts a fresh basis, so this bounds every run
+    if (re) a.template take<float>((size_t)nb_max * NR);
+    if (re && o->reorth == GP_REORTH_PINV) a.template take<float>((size_t)nb_max * NR);
+    const int nblk = (int)((N + kDotChunk - 1) / kDotChunk);
+    a.template take<double>((size_t)nblk * R * 3);
+    if (re) {
+        a.template take<double>((size_t)nblk * R * nb_max);
+        a.template take<double>((size_t)nb_max * R);
+    }
+    a.template take<double>((size_t)o->max_iter * R);
+    a.template take<double>((size_t)o->max_iter * R);
+    a.template take<double>((size_t)(o->max_iter + 1) * R);
+    a.template take<ColState>((size_t)R);
+    a.template take<int>(4);
+    a.template take<int>((size_t)R);
+    (void)ctx;
+    (void)rank;
+}
+
+int check_cg_args(const gp_hyp_t* hyp, int64_t N, int R, const gp_cg_opts_t* o) {
+    GPK_TRY(check_hyp(hyp));
+    if (!o || N < 1 || R < 1 || R > 64 || !(hyp->noise > 0.0)) return GP_ERR_INVALID;
+    if (o->max_iter < 1 || o->max_iter > 1000 || o->min_iter < 0 || !(o->tol >= 0.0)) return GP_ERR_INVALID;
+    if (o->algorithm != GP_CG_STABLE && o->algorithm != GP_CG_STANDARD) return GP_ERR_INVALID;
+    if (o->restarts < 0 || o->restarts > 16) return GP_ERR_INVALID;
+    if (o->check_precision < GP_PREC_FP32 || o->check_precision > GP_PREC_BF16) return GP_ERR_INVALID;
+    if (o->reorth < GP_REORTH_NONE || o->reorth > GP_REORTH_EUCLID) return GP_ERR_INVALID;
+    if (o->precision & GP_MVM_ADD_NOISE) return GP_ERR_INVALID;
+    return GP_OK;
+}
+
+}  // namespace
+
+size_t cg_workspace(const Ctx* ctx, const gp_hyp_t* hyp, int64_t N, int R, int rank, const gp_cg_opts_t* o) {
+    WsCounter c;
+    cg_layout(c, ctx, N, R, rank, o);
+    size_t s = c.off + kop_workspace(ctx, hyp, N, N, R, o->precision, true);
+    if (o->restarts > 0 && o->check_precision != (o->precision & 0xff))
+        s += kop_workspace(ctx, hyp, N, N, R, o->check_precision, true);
+    if (rank > 0) s += woodbury_workspace(ctx, N, rank, R);
+    return s;
+}
+
+int cg_run(Ctx* ctx, WsCarver& wc, const gp_hyp_t* hyp, const float* X, int64_t N, const float* B, int R,
+           float* U, const gp_precond_t* pc, const gp_cg_opts_t* o, gp_cg_stats_t* stats, cudaStream_t s) {
+    const int stable = o->algorithm == GP_CG_STABLE;
+    const int reorth = stable ? o->reorth : GP_REORTH_NONE;
+    const int passes = o->reorth_passes >= 2 ? 2 : 1;
+    const size_t NR = (size_t)N * R;
+    CgBufs b;
+    b.r = wc.take<float>(NR);
+    b.z = wc.take<float>(NR);
+    b.d = wc.take<float>(NR);
+    b.Kd = wc.take<float>(NR);
+    b.nb_max = o->max_iter + 1;
+    b.rho = reorth != GP_REORTH_NONE ? wc.take<float>((size_t)b.nb_max * NR) : nullptr;
+    b.zeta = reorth == GP_REORTH_PINV ? wc.take<float>((size_t)b.nb_max * NR) : nullptr;
+    b.nblk_dot = (int)((N + kDotChunk - 1) / kDotChunk);
+    b.dpart = wc.take<double>((size_t)b.nblk_dot * R * 3);
+    b.gpart = reorth != GP_REORTH_NONE ? wc.take<double>((size_t)b.nblk_dot * R * b.nb_max) : nullptr;
+    b.coef = reorth != GP_REORTH_NONE ? wc.take<double>((size_t)b.nb_max * R) : nullptr;
+    b.ahist = wc.take<double>((size_t)o->max_iter * R);
+    b.bhist = wc.take<double>((size_t)o->max_iter * R);
+    b.rhist = wc.take<double>((size_t)(o->max_iter + 1) * R);
+    b.st = wc.take<ColState>((size_t)R);
+    b.nact = wc.take<int>(4);
+    b.aflags = wc.take<int>((size_t)R);
+    if (!wc.ok) return GP_ERR_WORKSPACE;
+    const int rank = (pc && pc->rank > 0) ? pc->rank : 0;
+
+    KOp op;
+    GPK_TRY(kop_prepare(ctx, wc, op, hyp, X, N, X, N, R, o->precision, s));
+    KOp op_chk_own;
+    KOp* op_chk = &op;
+    if (o->restarts > 0 && o->check_precision != (o->precision & 0xff)) {
+        GPK_TRY(kop_prepare(ctx, wc, op_chk_own, hyp, X, N, X, N, R, o->check_precision, s));
+        op_chk = &op_chk_own;
+    }
+
+    const int vg = vec_grid(ctx, N);
+    const dim3 gcol((unsigned)vg, (unsigned)R);
+    const dim3 gdot((unsigned)b.nblk_dot, (unsigned)R);
+    auto launched = [&](int n) { ctx->launches += n; return cudaGetLastError() == cudaSuccess ? GP_OK : GP_ERR_CUDA; };
+    auto precond = [&](const float* W, float* Z, bool masked) -> int {
+        if (rank == 0) {
+            copy_active_kernel<<<gcol, 256, 0, s>>>(Z, W, N, masked ? b.st : nullptr);
+            return launched(1);
+        }
+        if (masked) {
+            active_flags_kernel<<<1, 64, 0, s>>>(b.st, R, b.aflags);
+            GPK_TRY(launched(1));
+        }
+        WsCarver wtmp = wc;   // Woodbury scratch beyond the solver's buffers
+        return woodbury_apply(ctx, wtmp, pc->L, pc->core, rank, hyp->noise, N, W, R, masked ? b.aflags : nullptr, Z, s);
+    };
+    auto dots = [&](const float* A, const float* Bv, bool masked) -> int {
+        dots_kernel<<<gdot, kDotThreads, 0, s>>>(A, Bv, N, b.nblk_dot, masked ? b.aflags : nullptr, b.dpart);
+        return launched(1);
+    };
+    auto scalar = [&](int mode, int k) -> int {
+        scalar_kernel<<<1, 1024, 0, s>>>(mode, stable, b.dpart, b.nblk_dot, R, b.st, k, o->tol, o->min_iter, b.ahist,
+                                         b.bhist, b.rhist, b.nact);
+        return launched(1);
+    };
+
+    // ---- initialisation (and re-initialisation on a true-residual restart) ----
+    GPK_TRY(dots(B, B, false));
+    GPK_TRY(scalar(SC_BNORM, 0));
+    auto start = [&](bool from_x, int k0) -> int {
+        if (from_x) {
+            // the first start uses the solve's MVM; a restart the check MVM
+            GPK_TRY(kop_apply(ctx, k0 > 0 ? *op_chk : op, U, R, b.Kd, N, true, s));
+            init_r_kernel<<<vg, 256, 0, s>>>(b.r, b.Kd, B, U, (int64_t)NR, 0);
+        } else {
+            init_r_kernel<<<vg, 256, 0, s>>>(b.r, nullptr, B, U, (int64_t)NR, 1);
+        }
+        GPK_TRY(launched(1));
+        GPK_TRY(precond(b.r, b.z, false));
+        GPK_TRY(dots(b.r, b.z, false));
+        GPK_TRY(scalar(SC_INIT, k0));
+        update_d_kernel<<<gcol, 256, 0, s>>>(b.d, b.z, b.r, N, b.st, 1, reorth, b.rho, b.zeta);
+        GPK_TRY(launched(1));
+        if (cudaMemcpyAsync(ctx->host_pinned, b.nact, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return GP_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return GP_ERR_CUDA;
+        return GP_OK;
+    };
+    GPK_TRY(start(o->x0_given != 0, 0));
+    int n_active = ctx->host_pinned[0];
+    int iters = 0, restarts = 0, nb0 = 0;   // nb0: first iteration of the current basis
+
+    int k = 0;
+    while (true) {
+        for (; k < o->max_iter && n_active > 0; ++k) {
+            // Kd = Ktilde d
+            GPK_TRY(kop_apply(ctx, op, b.d, R, b.Kd, N, true, s));
+            active_flags_kernel<<<1, 64, 0, s>>>(b.st, R, b.aflags);
+            GPK_TRY(launched(1));
+            GPK_TRY(dots(b.d, b.Kd, true));
+            GPK_TRY(scalar(SC_ALPHA, k));
+            update_xr_kernel<<<gcol, 256, 0, s>>>(U, b.r, b.d, b.Kd, N, b.st);
+            GPK_TRY(launched(1));
+            if (reorth != GP_REORTH_NONE) {
+                const int nb = k - nb0 + 1;   // basis vectors r_0 .. r_k of this run
+                const float* ZB = reorth == GP_REORTH_PINV ? b.zeta : b.rho;
+                for (int p = 0; p < passes; ++p) {
+                    gram_kernel<<<gdot, kDotThreads, 0, s>>>(ZB, nb, R, b.r, N, b.nblk_dot, b.st, b.gpart);
+                    gram_finalize_kernel<<<(nb * R + 255) / 256, 256, 0, s>>>(b.gpart, b.nblk_dot, nb, R, b.st,
+                                                                             b.coef);
+                    reorth_update_kernel<<<gcol, 256, 0, s>>>(b.rho, nb, R, b.coef, b.r, N, b.st);
+                    GPK_TRY(launched(3));
+                }
+            }
+            GPK_TRY(precond(b.r, b.z, true));
+            GPK_TRY(dots(b.r, b.z, true));
+            GPK_TRY(scalar(SC_BETA, k));
+            const size_t slot = (size_t)(k - nb0 + 1);
+            float* rho_k = b.rho ? b.rho + slot * NR : nullptr;
+            float* zeta_k = b.zeta ? b.zeta + slot * NR : nullptr;
+            update_d_kernel<<<gcol, 256, 0, s>>>(b.d, b.z, b.r, N, b.st, 0, reorth, rho_k, zeta_k);
+            GPK_TRY(launched(1));
+            if (cudaMemcpyAsync(ctx->host_pinned, b.nact, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+                return GP_ERR_CUDA;
+            if (cudaStreamSynchronize(s) != cudaSuccess) return GP_ERR_CUDA;
+            n_active = ctx->host_pinned[0];
+            iters = k + 1;
+        }
+        if (restarts >= o->restarts || k >= o->max_iter) break;
+        // True-residual check: recompute r = K x - b; columns above tol restart.
+        ++restarts;
+        nb0 = k;
+        GPK_TRY(start(true, k));
+        n_active = ctx->host_pinned[0];
+        if (n_active == 0) break;
+    }
+
+    // ---- statistics ----
+    ColState* hs = (ColState*)malloc(sizeof(ColState) * R);
+    if (!hs) return GP_ERR_OOM;
+    cudaError_t ce = cudaMemcpyAsync(hs, b.st, sizeof(ColState) * R, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess && stats) {
+        if (stats->alpha) ce = cudaMemcpyAsync(stats->alpha, b.ahist, sizeof(double) * o->max_iter * R, cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess && stats->beta)
+            ce = cudaMemcpyAsync(stats->beta, b.bhist, sizeof(double) * o->max_iter * R, cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess && stats->resid_hist)
+            ce = cudaMemcpyAsync(stats->resid_hist, b.rhist, sizeof(double) * (o->max_iter + 1) * R,
+                                 cudaMemcpyDeviceToHost, s);
+    }
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) {
+        free(hs);
+        return GP_ERR_CUDA;
+    }
+    int conv = 0, brk = 0, maxit = 0;
+    for (int c = 0; c < R; ++c) {
+        if (hs[c].breakdown) ++brk;
+        else if (hs[c].relres <= o->tol) ++conv;
+        if (hs[c].iters > maxit) maxit = hs[c].iters;
+    }
+    if (stats) {
+        stats->iters = iters;
+        stats->converged = conv;
+        stats->breakdowns = brk;
+        stats->restarts = restarts;
+        for (int c = 0; c < R; ++c) {
+            if (stats->col_iters) stats->col_iters[c] = hs[c].iters;
+            if (stats->rel_resid) stats->rel_resid[c] = hs[c].relres;
+            if (stats->gamma0) stats->gamma0[c] = hs[c].gamma0;
+        }
+    }
+    free(hs);
+    (void)maxit;
+    if (brk > 0) return GP_ERR_BREAKDOWN;
+    return conv == R ? GP_OK : GP_ERR_NOT_CONVERGED;
+}
+
+}  // namespace gpk
+
+extern "C" {
+
+size_t gp_cg_workspace_size(const gp_hyp_t* hyp, int64_t N, int R, int rank, const gp_cg_opts_t* opts) {
+    if (gpk::check_cg_args(hyp, N, R, opts) != GP_OK) return 0;
+    gpk::Ctx probe;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&probe.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) probe.num_sms = 148;
+    return gpk::cg_workspace(&probe, hyp, N, R, rank, opts);
+}
+
+int gp_cg_solve(gp_ctx* ctx, const gp_hyp_t* hyp, const float* X, int64_t N, const float* B, int R, float* U,
+                const gp_precond_t* precond, const gp_cg_opts_t* opts, gp_cg_stats_t* stats, void* stream) {
+    if (!ctx || !X || !B || !U) return GP_ERR_INVALID;
+    GPK_TRY(gpk::check_cg_args(hyp, N, R, opts));
+    if (precond && precond->rank > 0 && (!precond->L || !precond->core || precond->rank > 512)) return GP_ERR_INVALID;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess) return GP_ERR_CUDA;
+    gpk::WsCarver wc(ctx->ws, ctx->ws_bytes);
+    int st = gpk::cg_run(ctx, wc, hyp, X, N, B, R, U, precond, opts, stats, (cudaStream_t)stream);
+    if (prev != ctx->device) cudaSetDevice(prev);
+    return st;
+}
+
+}  // extern "C"

@@ -23,7 +23,15 @@ struct Ctx {
     int* dev_err = nullptr;       // device error word (own allocation, 64 B)
     int* host_pinned = nullptr;   // pinned host scratch (flags, small readbacks), 4 KB
     int64_t launches = 0;         // kernels launched through this context
+    // CUDA-event timing of the tensor-core MVM launches (gp_ctx_profile)
+    static constexpr int kProfMax = 8192;
+    bool prof = false;
+    bool prof_ev_ready = false;
+    int prof_n = 0;
+    cudaEvent_t prof_ev[2 * kProfMax];
 };
+void prof_begin(Ctx* ctx, cudaStream_t s);
+void prof_end(Ctx* ctx, cudaStream_t s);
 
 // Bump allocator over the context workspace (alignment 256 B).
 struct WsCarver {
@@ -117,6 +125,8 @@ struct MvmArgs {
     const float* Vnoise;       // FP32 V for the noise term (Nc x R col-major) or null
     float* out;                // Nr x R col-major
     int64_t ld_out;
+    float diag_coef = 0.0f;    // square operator: the exact a^2 v_i of the diagonal is
+                               // added here and the on-chip diagonal is skipped
 };
 
 // Tensor-core engine (kmvm_tc.cu).
@@ -151,6 +161,7 @@ int launch_split_reduce(Ctx* ctx, const float* partial, int n_split, int64_t ld_
 // every apply casts V and runs the engine.
 struct KOp {
     int kernel = 0, prec = 0, flags = 0, d = 0, R_max = 0;
+    bool square = false;
     int64_t Nr = 0, Nc = 0;
     float a2 = 1.0f, noise = 0.0f;
     OperandLayout lay;

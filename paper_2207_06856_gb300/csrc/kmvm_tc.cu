@@ -53,6 +53,8 @@ struct TcParams {
     int vsplit;                  // 1: Vt carries hi rows then lo rows
     int psplit;                  // 1: the kernel tile is carried as hi (in place) + lo (kPLoCol)
     int stages;                  // shared-memory ring depth (<= kStages)
+    int diag;                    // square operator: P_ii is set to 0 on chip and the exact
+                                 // a^2 v_i is added with the noise term (k(x, x) = 1)
     int64_t Nr;
     float noise;                 // sigma^2, 0 = no noise term
     const float* Vnoise;         // FP32 V (ld = ld_v) for the noise term
@@ -254,6 +256,7 @@ __device__ void tc_epilogue(const TcParams& p, TcBarriers& bars, uint32_t tmem, 
             if (!ptx::mbar_wait(&bars.s_full[b], (g >> 1) & 1, p.limit_ns)) { ok = false; break; }
             ptx::tc_fence_after();
             const uint32_t tS = tmem + lane_off + b * 128u;
+            const bool dtile = p.diag && (j0 + (int)t == it);
 #pragma unroll 1
             for (int h = 0; h < 4; ++h) {
                 uint32_t r[32];
@@ -263,8 +266,13 @@ __device__ void tc_epilogue(const TcParams& p, TcBarriers& bars, uint32_t tmem, 
                 uint32_t pl[16];
 #pragma unroll
                 for (int e = 0; e < 16; ++e) {
-                    const float k0 = kernel_from_s<KIND>(__uint_as_float(r[2 * e]));
-                    const float k1 = kernel_from_s<KIND>(__uint_as_float(r[2 * e + 1]));
+                    float k0 = kernel_from_s<KIND>(__uint_as_float(r[2 * e]));
+                    float k1 = kernel_from_s<KIND>(__uint_as_float(r[2 * e + 1]));
+                    if (dtile) {
+                        const int col = h * 32 + 2 * e;
+                        if (col == row) k0 = 0.0f;
+                        if (col + 1 == row) k1 = 0.0f;
+                    }
                     pk[e] = pack2<BF16>(k0, k1);
                     if constexpr (PSPLIT) pl[e] = pack2<BF16>(k0 - unpack_lo<BF16>(pk[e]), k1 - unpack_hi<BF16>(pk[e]));
                 }
@@ -446,7 +454,8 @@ int launch_kmvm_tc(Ctx* ctx, const TcPlan& plan, const OperandLayout& L, const M
     prm.stages = tc_stages(plan.k_pad, plan.R_pad, L.vsplit);
     if (prm.stages < 2) return GP_ERR_UNSUPPORTED;
     prm.Nr = a.Nr;
-    prm.noise = a.noise;
+    prm.noise = a.noise + a.diag_coef;
+    prm.diag = a.diag_coef != 0.0f ? 1 : 0;
     prm.Vnoise = a.Vnoise;
     prm.ld_v = a.Nc;
     prm.outscale = outscale;
@@ -458,6 +467,7 @@ int launch_kmvm_tc(Ctx* ctx, const TcPlan& plan, const OperandLayout& L, const M
     prm.limit_ns = kWaitLimitNs;
     const int bf = (L.prec == GP_PREC_BF16) ? 1 : 0;
     cudaError_t e = cudaErrorInvalidValue;
+    prof_begin(ctx, s);
 #define GPK_TC_CASE(K)                                                                  \
     case K:                                                                             \
         e = bf ? (L.psplit ? launch_tc_typed<K, 1, 1>(plan, prm, tmA, tmB, tmV, s)      \
@@ -472,11 +482,12 @@ int launch_kmvm_tc(Ctx* ctx, const TcPlan& plan, const OperandLayout& L, const M
         default: return GP_ERR_INVALID;
     }
 #undef GPK_TC_CASE
+    prof_end(ctx, s);
     ctx->launches++;
     if (e != cudaSuccess) return GP_ERR_CUDA;
     if (plan.n_split > 1)
         return launch_split_reduce(ctx, partial, plan.n_split, plan.Nr_pad, a.Nr, a.R, plan.R_pad, outscale, 0.0f,
-                                   a.noise, a.Vnoise, a.Nc, a.out, a.ld_out, s);
+                                   prm.noise, a.Vnoise, a.Nc, a.out, a.ld_out, s);
     return GP_OK;
 }
 

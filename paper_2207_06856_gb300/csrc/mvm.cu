@@ -114,6 +114,7 @@ int kop_prepare(Ctx* ctx, WsCarver& wc, KOp& op, const gp_hyp_t* hyp, const floa
                 const float* Xc, int64_t Nc, int R, int flags, cudaStream_t s) {
     GPK_TRY(kop_plan(ctx, op, hyp, Nr, Nc, R, flags));
     const bool square = (Xr == Xc && Nr == Nc);
+    op.square = square;
     ScaleVec inv;
     memset(&inv, 0, sizeof(inv));
     const float c = kernel_input_scale(hyp->kernel);
@@ -170,6 +171,7 @@ int kop_apply(Ctx* ctx, KOp& op, const float* V, int R, float* out, int64_t ld_o
         a.Vnoise = V + (int64_t)c0 * op.Nc;
         a.out = out + (int64_t)c0 * ld_out;
         a.ld_out = ld_out;
+        a.diag_coef = (op.square && op.prec != GP_PREC_FP32) ? op.a2 : 0.0f;
         const float* Vc = V + (int64_t)c0 * op.Nc;
         if (op.prec == GP_PREC_FP32) {
             SimtPlan pl = op.sp;

@@ -52,6 +52,30 @@ class GPKError(RuntimeError):
         super().__init__(f"{what}: {strerror(status)} ({status})" if what else f"{strerror(status)} ({status})")
 
 
+CG_STABLE, CG_STANDARD = 0, 1
+REORTH_NONE, REORTH_PINV, REORTH_EUCLID = 0, 1, 2
+REORTH = {"none": REORTH_NONE, "pinv": REORTH_PINV, "euclid": REORTH_EUCLID}
+
+
+class _Precond(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_void_p), ("core", ctypes.c_void_p), ("rank", ctypes.c_int)]
+
+
+class _CgOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("min_iter", ctypes.c_int),
+                ("precision", ctypes.c_int), ("algorithm", ctypes.c_int), ("reorth", ctypes.c_int),
+                ("reorth_passes", ctypes.c_int), ("x0_given", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("check_precision", ctypes.c_int)]
+
+
+class _CgStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("breakdowns", ctypes.c_int),
+                ("restarts", ctypes.c_int),
+                ("col_iters", ctypes.POINTER(ctypes.c_int)), ("rel_resid", ctypes.POINTER(ctypes.c_double)),
+                ("alpha", ctypes.POINTER(ctypes.c_double)), ("beta", ctypes.POINTER(ctypes.c_double)),
+                ("gamma0", ctypes.POINTER(ctypes.c_double)), ("resid_hist", ctypes.POINTER(ctypes.c_double))]
+
+
 class _Hyp(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("d", ctypes.c_int),
                 ("lengthscale", ctypes.POINTER(ctypes.c_float)),
@@ -77,6 +101,17 @@ def _declare(lib):
         "gp_kmvm_workspace_size": (_c_size, [ctypes.POINTER(_Hyp), _c_i64, _c_i64, _c_int, _c_int]),
         "gp_kmvm": (_c_int, [_c_void_p, ctypes.POINTER(_Hyp), _c_void_p, _c_i64, _c_void_p, _c_i64,
                              _c_void_p, _c_int, _c_void_p, _c_int, _c_void_p]),
+        "gp_ctx_profile": (_c_int, [_c_void_p, _c_int]),
+        "gp_ctx_profile_read": (_c_int, [_c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_c_i64)]),
+        "gp_measure_peaks": (_c_int, [_c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double), _c_void_p]),
+        "gp_pivchol_workspace_size": (_c_size, [ctypes.POINTER(_Hyp), _c_i64, _c_int]),
+        "gp_pivchol_precond": (_c_int, [_c_void_p, ctypes.POINTER(_Hyp), _c_void_p, _c_i64, _c_int, _c_void_p,
+                                        _c_void_p, _c_void_p, ctypes.POINTER(_c_int), _c_void_p]),
+        "gp_cg_workspace_size": (_c_size, [ctypes.POINTER(_Hyp), _c_i64, _c_int, _c_int, ctypes.POINTER(_CgOpts)]),
+        "gp_cg_solve": (_c_int, [_c_void_p, ctypes.POINTER(_Hyp), _c_void_p, _c_i64, _c_void_p, _c_int, _c_void_p,
+                                 ctypes.POINTER(_Precond), ctypes.POINTER(_CgOpts), ctypes.POINTER(_CgStats),
+                                 _c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -185,6 +220,24 @@ class Context:
     def check(self, stream=None):
         _check(lib().gp_ctx_check(self._p, _c_void_p(_stream_ptr(stream))), "device error")
 
+    def profile(self, enable: bool = True):
+        """Record CUDA events around every tensor-core MVM launch."""
+        _check(lib().gp_ctx_profile(self._p, 1 if enable else 0), "gp_ctx_profile")
+
+    def profile_read(self):
+        """(summed milliseconds, launch count) of the profiled MVM launches; resets."""
+        ms = ctypes.c_double(0.0)
+        n = _c_i64(0)
+        _check(lib().gp_ctx_profile_read(self._p, ctypes.byref(ms), ctypes.byref(n)), "gp_ctx_profile_read")
+        return float(ms.value), int(n.value)
+
+    def measure_peaks(self, stream=None) -> dict:
+        """Measured throughput (ops/s) of ex2, sqrt (special function units) and FP32 FMA."""
+        e, q, f = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().gp_measure_peaks(self._p, ctypes.byref(e), ctypes.byref(q), ctypes.byref(f),
+                                      _stream_ptr(stream)), "gp_measure_peaks")
+        return {"ex2_per_s": e.value, "sqrt_per_s": q.value, "ffma_per_s": f.value}
+
 
 def kmvm_workspace_size(hyp: Hyper, Nr: int, Nc: int, R: int, flags: int) -> int:
     h = hyp.c()
@@ -214,3 +267,90 @@ def kmvm(ctx: Context, hyp: Hyper, Xr, V, Xc=None, precision="fp16", add_noise=F
                        _dev_ptr(V, "V", (R, Nc)), R, _dev_ptr(out, "out", (R, Nr)), fl, _stream_ptr(stream))
     _check(st, "gp_kmvm")
     return out
+
+
+@dataclass
+class Precond:
+    """Pivoted-Cholesky preconditioner P = L L^T + sigma^2 I (Eq. woodbury).
+    L: (rank, N) float32 CUDA tensor (N x rank column-major); core: the lower
+    Cholesky factor of I + sigma^-2 L^T L as a (rank, rank) float64 CUDA
+    tensor holding it column-major (core.T is the factor); piv: int32 pivots."""
+    L: object
+    core: object
+    piv: object
+    rank: int
+
+    def c(self) -> _Precond:
+        return _Precond(int(self.L.data_ptr()), int(self.core.data_ptr()), int(self.rank))
+
+
+def pivchol(ctx: Context, hyp: Hyper, X, rank: int, stream=None) -> Precond:
+    """gp_pivchol_precond: rank-k pivoted Cholesky of K(X, X) and its FP64 Woodbury core."""
+    import torch
+    N, d = X.shape
+    h = hyp.c()
+    need = int(lib().gp_pivchol_workspace_size(ctypes.byref(h), N, int(rank)))
+    if need == 0:
+        raise GPKError(GP_ERR_INVALID, "gp_pivchol_workspace_size")
+    if need > ctx.workspace_bytes:
+        ctx.reserve(need)
+    L = torch.empty((rank, N), dtype=torch.float32, device=X.device)
+    piv = torch.empty((rank,), dtype=torch.int32, device=X.device)
+    core = torch.zeros((rank * rank,), dtype=torch.float64, device=X.device)
+    rk = _c_int(0)
+    st = lib().gp_pivchol_precond(ctx.ptr, ctypes.byref(h), _dev_ptr(X, "X", (N, d)), N, int(rank), int(L.data_ptr()),
+                                  int(piv.data_ptr()), int(core.data_ptr()), ctypes.byref(rk), _stream_ptr(stream))
+    _check(st, "gp_pivchol_precond")
+    k = int(rk.value)
+    return Precond(L[:k], core[:k * k].view(k, k), piv[:k], k)
+
+
+def cg_solve(ctx: Context, hyp: Hyper, X, B, precond: Precond | None = None, tol: float = 1e-2,
+             max_iter: int = 50, min_iter: int = 0, precision="fp16", algorithm: str = "stable",
+             reorth: str = "pinv", reorth_passes: int = 1, U=None, flags: int = 0, restarts: int = 4,
+             check_precision="fp32", stream=None):
+    """gp_cg_solve: (K + sigma^2 I) U = B.  B (R, N) -> (U (R, N), status, info).
+    info holds the per-column iterations, relative residuals, alpha/beta
+    histories (numpy arrays) and gamma_0.  status is GP_OK,
+    GP_ERR_NOT_CONVERGED or GP_ERR_BREAKDOWN (other errors raise)."""
+    import torch
+    N, d = X.shape
+    R = B.shape[0]
+    prec = (PRECISIONS[precision] if isinstance(precision, str) else int(precision)) | int(flags)
+    opts = _CgOpts(float(tol), int(max_iter), int(min_iter), prec,
+                   CG_STABLE if algorithm == "stable" else CG_STANDARD,
+                   REORTH[reorth] if isinstance(reorth, str) else int(reorth), int(reorth_passes),
+                   1 if U is not None else 0, int(restarts),
+                   PRECISIONS[check_precision] if isinstance(check_precision, str) else int(check_precision))
+    h = hyp.c()
+    rank = precond.rank if precond is not None else 0
+    need = int(lib().gp_cg_workspace_size(ctypes.byref(h), N, R, rank, ctypes.byref(opts)))
+    if need == 0:
+        raise GPKError(GP_ERR_INVALID, "gp_cg_workspace_size")
+    if need > ctx.workspace_bytes:
+        ctx.reserve(need)
+    if U is None:
+        U = torch.empty((R, N), dtype=torch.float32, device=B.device)
+    col_iters = np.zeros(R, np.int32)
+    rel = np.zeros(R, np.float64)
+    al = np.zeros(max_iter * R, np.float64)
+    be = np.zeros(max_iter * R, np.float64)
+    g0 = np.zeros(R, np.float64)
+    rh = np.zeros((max_iter + 1) * R, np.float64)
+    P = ctypes.POINTER
+    stats = _CgStats(0, 0, 0, 0, col_iters.ctypes.data_as(P(ctypes.c_int)), rel.ctypes.data_as(P(ctypes.c_double)),
+                     al.ctypes.data_as(P(ctypes.c_double)), be.ctypes.data_as(P(ctypes.c_double)),
+                     g0.ctypes.data_as(P(ctypes.c_double)), rh.ctypes.data_as(P(ctypes.c_double)))
+    pc = precond.c() if precond is not None else _Precond(None, None, 0)
+    st = lib().gp_cg_solve(ctx.ptr, ctypes.byref(h), _dev_ptr(X, "X", (N, d)), N, _dev_ptr(B, "B", (R, N)), R,
+                           _dev_ptr(U, "U", (R, N)), ctypes.byref(pc), ctypes.byref(opts), ctypes.byref(stats),
+                           _stream_ptr(stream))
+    if st not in (GP_OK, GP_ERR_NOT_CONVERGED, GP_ERR_BREAKDOWN):
+        _check(st, "gp_cg_solve")
+    it = int(stats.iters)
+    info = {"iters": it, "converged": int(stats.converged), "breakdowns": int(stats.breakdowns),
+            "restarts": int(stats.restarts),
+            "col_iters": col_iters, "rel_resid": rel, "gamma0": g0,
+            "alpha": al.reshape(max_iter, R)[:it], "beta": be.reshape(max_iter, R)[:it],
+            "resid_hist": rh.reshape(max_iter + 1, R)[:it + 1]}
+    return U, st, info

@@ -78,7 +78,7 @@ def plain(N: int = 2048, seed: int = 0) -> Workload:
     y = np.sin(2.0 * math.pi * X.mean(axis=1)) + 0.1 * rng.standard_normal(N)
     return Workload("plain", X.astype(np.float32), y.astype(np.float32),
                     np.zeros((0, N), np.float32), RBF, np.full(d, 0.5, np.float32),
-                    1.0, 0.01, 20, 1e-4, max_iter=200)
+                    1.0, 0.01, 20, 1e-4, max_iter=500)
 
 
 def precision(N: int = 65536, seed: int = 0, kernel: int = RBF, M: int = 16) -> Workload:
@@ -92,7 +92,7 @@ def precision(N: int = 65536, seed: int = 0, kernel: int = RBF, M: int = 16) -> 
     y = np.sin(2.0 * math.pi * X.mean(axis=1)) + 0.1 * rng.standard_normal(N)
     Z = rademacher(rng, M, N)
     return Workload("precision", X.astype(np.float32), y.astype(np.float32), Z, kernel,
-                    np.full(d, 1.0, np.float32), 1.0, 0.05, 100, 1e-2, max_iter=50)
+                    np.full(d, 1.0, np.float32), 1.0, 0.05, 100, 1e-2, max_iter=1000)
 
 
 def _gmm(rng: np.random.Generator, N: int, d: int, comps: int, mean_scale: float,

@@ -1,0 +1,184 @@
+"""Pivoted-Cholesky preconditioner (gp_pivchol_precond) and CG (gp_cg_solve,
+Alg. 1 / Alg. 2) on the GPU against the FP64 oracle.
+
+Solves are judged by their FP64-recomputed relative residual
+||Ktilde U - B|| / ||B|| per column (the trajectory itself is not pinned)."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2207_06856_gb300 import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+KNAME = {0: "rbf", 1: "matern32", 2: "matern12", 3: "matern52"}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2207_06856_gb300 import gpk
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = gpk.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+
+
+def _ohyp(w):
+    return O.Hyp(KNAME[w.kernel], w.lengthscale, w.outputscale, w.noise)
+
+
+def test_pivchol_invariants(ctx):
+    from paper_2207_06856_gb300 import gpk
+    X, _, kern, ls, a2, s2 = workloads.random_problem(1500, 5, 1, seed=21, kernel=1)
+    hyp = gpk.Hyper(kern, ls, a2, s2)
+    pc = gpk.pivchol(ctx, hyp, _dev(X), 30)
+    ctx.check()
+    assert pc.rank == 30
+    L = pc.L.cpu().numpy().astype(np.float64).T          # N x k
+    piv = pc.piv.cpu().numpy()
+    oh = O.Hyp("matern32", ls, a2, s2)
+    K = O.kernel_matrix(X, X, oh)
+    assert piv[0] == 0 and len(set(piv.tolist())) == 30
+    # interpolation: (L L^T)[p, :] = K[p, :] for the pivots (FP32 rows)
+    assert np.max(np.abs((L @ L.T)[piv] - K[piv])) < 2e-4 * a2
+    rem = np.diag(K) - np.sum(L * L, axis=1)
+    assert rem.min() > -1e-4
+    # the first pivots agree with the FP64 oracle (later ones may swap on near-ties)
+    _, opiv = O.pivoted_cholesky(X, oh, 8)
+    assert list(piv[:8]) == list(opiv[:8])
+    # core: lower Cholesky factor of I + L^T L / sigma^2, in FP64
+    Lc = pc.core.cpu().numpy().T
+    C = np.eye(30) + (L.T @ L) / s2
+    np.testing.assert_allclose(Lc @ Lc.T, C, rtol=1e-5, atol=1e-5 * np.abs(C).max())
+
+
+@pytest.mark.parametrize("alg", ["stable", "standard"])
+def test_plain_config_fp32(ctx, alg):
+    """Plain workload: N = 2048, d = 8, RBF l = 0.5, sigma^2 = 0.01, rank 20,
+    tol 1e-4, FP32 on the GPU vs the FP64 oracle."""
+    from paper_2207_06856_gb300 import gpk
+    w = workloads.plain()
+    hyp = gpk.Hyper(w.kernel, w.lengthscale, w.outputscale, w.noise)
+    X = _dev(w.X)
+    pc = gpk.pivchol(ctx, hyp, X, w.rank)
+    B = w.rhs()
+    U, st, info = gpk.cg_solve(ctx, hyp, X, _dev(B), pc, tol=w.tol, max_iter=w.max_iter, precision="fp32",
+                               algorithm=alg, reorth="pinv" if alg == "stable" else "none", restarts=4)
+    ctx.check()
+    assert st == gpk.GP_OK, info
+    res = O.relative_residual(w.X, U.cpu().numpy().T, B.T, _ohyp(w))
+    assert res.max() <= w.tol, res
+    ref = O.cholesky_solve(w.X, _ohyp(w), B.T.astype(np.float64))
+    err = np.linalg.norm(U.cpu().numpy().T - ref) / np.linalg.norm(ref)
+    assert err < 1e-2
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16", "fp32"])
+@pytest.mark.parametrize("kern", [0, 1])
+def test_stable_cg_precision_workload_small(ctx, prec, kern):
+    """The precision workload at N = 6000 (1 + 16 RHS, rank 100 preconditioner):
+    the FP64 residual of every column is <= 1e-2."""
+    from paper_2207_06856_gb300 import gpk
+    w = workloads.precision(N=6000, kernel=kern)
+    hyp = gpk.Hyper(w.kernel, w.lengthscale, w.outputscale, w.noise)
+    X = _dev(w.X)
+    pc = gpk.pivchol(ctx, hyp, X, w.rank)
+    B = w.rhs()
+    U, st, info = gpk.cg_solve(ctx, hyp, X, _dev(B), pc, tol=w.tol, max_iter=400, precision=prec)
+    ctx.check()
+    assert st == gpk.GP_OK, (info["col_iters"], info["rel_resid"])
+    res = O.relative_residual(w.X, U.cpu().numpy().T, B.T, _ohyp(w))
+    assert res.max() <= w.tol, res
+
+
+def test_reorth_modes_and_standard_agree_on_small_problem(ctx):
+    """All variants reach the same solution on a well-conditioned small problem."""
+    from paper_2207_06856_gb300 import gpk
+    X, V, kern, ls, a2, s2 = workloads.random_problem(900, 4, 3, seed=22, noise=0.1)
+    hyp = gpk.Hyper(kern, ls, a2, s2)
+    Xd, Bd = _dev(X), _dev(V)
+    pc = gpk.pivchol(ctx, hyp, Xd, 10)
+    ref = O.cholesky_solve(X, O.Hyp("rbf", ls, a2, s2), V.T.astype(np.float64))
+    for alg, ro, pre in [("stable", "pinv", pc), ("stable", "euclid", None), ("stable", "none", pc),
+                         ("standard", "none", pc), ("stable", "pinv", None)]:
+        U, st, info = gpk.cg_solve(ctx, hyp, Xd, Bd, pre, tol=1e-6, max_iter=300, precision="fp32", algorithm=alg,
+                                   reorth=ro, reorth_passes=2)
+        ctx.check()
+        assert st == gpk.GP_OK, (alg, ro, info["rel_resid"])
+        err = np.linalg.norm(U.cpu().numpy().T - ref) / np.linalg.norm(ref)
+        assert err < 1e-4, (alg, ro, err)
+
+
+def test_cg_trajectory_matches_oracle_alg2(ctx):
+    """Parity unpinned beyond the solution, but in FP32 the first step sizes of
+    Alg. 2 follow the FP64 oracle's closely."""
+    from paper_2207_06856_gb300 import gpk
+    X, V, kern, ls, a2, s2 = workloads.random_problem(700, 3, 1, seed=23, noise=0.05)
+    hyp = gpk.Hyper(kern, ls, a2, s2)
+    Xd = _dev(X)
+    pc = gpk.pivchol(ctx, hyp, Xd, 8)
+    U, st, info = gpk.cg_solve(ctx, hyp, Xd, _dev(V), pc, tol=1e-5, max_iter=100, precision="fp32", restarts=0)
+    oh = O.Hyp("rbf", ls, a2, s2)
+    piv_np = pc.piv.cpu().numpy()
+    L64, _ = O.pivoted_cholesky(X, oh, 8)
+    Kt = O.ktilde_dense(X, oh)
+    ores = O.cg_stable(lambda v: Kt @ v, V[0].astype(np.float64),
+                       precond=lambda r: O.precond_apply(L64, s2, r), tol=1e-5, max_iter=100)
+    assert list(piv_np) == list(O.pivoted_cholesky(X, oh, 8)[1])
+    n = min(5, len(ores.alphas), info["alpha"].shape[0])
+    np.testing.assert_allclose(info["alpha"][:n, 0], ores.alphas[:n], rtol=1e-3)
+    np.testing.assert_allclose(info["beta"][:n, 0], ores.betas[:n], rtol=1e-2)
+    assert abs(info["iters"] - ores.iters) <= 3
+    assert abs(info["gamma0"][0] - ores.gamma0) < 1e-4 * ores.gamma0
+
+
+def test_cg_edge_cases(ctx):
+    from paper_2207_06856_gb300 import gpk
+    # N = 1: Ktilde = a^2 + sigma^2, one step solves it
+    hyp = gpk.Hyper(0, np.ones(2), 1.5, 0.5)
+    X = _dev(np.zeros((1, 2), np.float32))
+    B = _dev(np.array([[3.0]], np.float32))
+    U, st, info = gpk.cg_solve(ctx, hyp, X, B, None, tol=1e-6, max_iter=5, precision="fp16")
+    assert st == gpk.GP_OK
+    assert abs(U.item() - 3.0 / 2.0) < 1e-5
+    # zero right-hand side: nothing to do, U = 0
+    Xn, V, kern, ls, a2, s2 = workloads.random_problem(500, 3, 2, seed=24)
+    V[1] = 0.0
+    hyp = gpk.Hyper(kern, ls, a2, s2)
+    U, st, info = gpk.cg_solve(ctx, hyp, _dev(Xn), _dev(V), None, tol=1e-3, max_iter=100, precision="fp32")
+    assert np.all(U.cpu().numpy()[1] == 0.0)
+    # max_iter reached -> NOT_CONVERGED, iterate still returned
+    U, st, info = gpk.cg_solve(ctx, hyp, _dev(Xn), _dev(V[:1]), None, tol=1e-12, max_iter=2, precision="fp32")
+    assert st == gpk.GP_ERR_NOT_CONVERGED and info["iters"] == 2
+    # warm start from the solution: converged before the first step
+    ref = O.cholesky_solve(Xn, O.Hyp("rbf", ls, a2, s2), V[:1].T.astype(np.float64)).T.astype(np.float32)
+    U0 = _dev(ref)
+    U, st, info = gpk.cg_solve(ctx, hyp, _dev(Xn), _dev(V[:1]), None, tol=1e-4, max_iter=10, precision="fp32", U=U0)
+    assert st == gpk.GP_OK and info["iters"] <= 1
+    ctx.check()
+
+
+def test_precision_workload_full_size_fp16(ctx):
+    """The benchmark solve: N = 65,536, d = 8, RBF, 1 + 16 RHS, rank-100
+    preconditioner, FP16 tensor-core MVM, stable CG to 1e-2; the FP64 residual on
+    1024 sampled rows is <= 1e-2 for every column."""
+    from paper_2207_06856_gb300 import gpk
+    w = workloads.precision()
+    hyp = gpk.Hyper(w.kernel, w.lengthscale, w.outputscale, w.noise)
+    X = _dev(w.X)
+    pc = gpk.pivchol(ctx, hyp, X, w.rank)
+    B = w.rhs()
+    U, st, info = gpk.cg_solve(ctx, hyp, X, _dev(B), pc, tol=w.tol, max_iter=w.max_iter, precision="fp16")
+    ctx.check()
+    assert st == gpk.GP_OK, (info["col_iters"], info["rel_resid"])
+    rows = np.sort(np.random.default_rng(25).choice(w.N, 1024, replace=False))
+    res = O.relative_residual(w.X, U.cpu().numpy().T, B.T, _ohyp(w), rows=rows)
+    assert res.max() <= w.tol, res
