@@ -145,6 +145,29 @@ GPK_API int gp_kmvm(gp_ctx* ctx, const gp_hyp_t* hyp,
             const float* Xr, int64_t Nr, const float* Xc, int64_t Nc,
             const float* V, int R, float* out, int flags, void* stream);
 
+/* ---- kernel MVM without any allocation -------------------------------------
+ * gp_kmvm_noalloc computes exactly what gp_kmvm computes (same arguments and
+ * flags, same kernels and results), for callers that cannot allocate device
+ * memory: host applications that own every device allocation through their
+ * own pool and forbid side allocations, latency-critical loops that cannot
+ * afford an allocation, plugins handed device pointers but no way to allocate.
+ * It takes no context and allocates nothing; the caller still passes the
+ * inputs and the output.  Its scratch is a fixed array of
+ * GPK_NOALLOC_SCRATCH_BYTES in device memory, held by every GPU that loads the
+ * library until the process exits.  A problem whose scratch need (as
+ * gp_kmvm_workspace_size reports for these arguments) exceeds that size is
+ * rejected with GP_ERR_WORKSPACE.
+ * - The first call on a device looks up the array's device address; make
+ *   that first call before any stream capture.
+ * - Every call shares the array: calls whose work overlaps on the GPU (for
+ *   example on two unordered streams) race and corrupt each other.
+ * - Asynchronous on `stream` like gp_kmvm; a device-side wait that runs out
+ *   is recorded in the shared array, not reported by this call.
+ * The paper has no counterpart: this is a deployment variant of Eq. mvm. */
+#define GPK_NOALLOC_SCRATCH_BYTES (16u << 20)
+GPK_API int gp_kmvm_noalloc(const gp_hyp_t* hyp, const float* Xr, int64_t Nr, const float* Xc, int64_t Nc,
+                            const float* V, int R, float* out, int flags, void* stream);
+
 /* ---- S3: pivoted-Cholesky preconditioner (Sec. 4.2, Eq. woodbury) ---------
  * k = rank steps of partial pivoted Cholesky of K (no noise) from kernel rows
  * K e_p and the constant diagonal a^2: pivot = argmax of the remaining

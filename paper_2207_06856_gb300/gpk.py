@@ -354,3 +354,26 @@ def cg_solve(ctx: Context, hyp: Hyper, X, B, precond: Precond | None = None, tol
             "alpha": al.reshape(max_iter, R)[:it], "beta": be.reshape(max_iter, R)[:it],
             "resid_hist": rh.reshape(max_iter + 1, R)[:it + 1]}
     return U, st, info
+
+
+def kmvm_noalloc(hyp: Hyper, Xr, V, Xc=None, precision="fp16", add_noise=False, flags=0, out=None, stream=None):
+    """gp_kmvm_noalloc: the same product as kmvm, with no context and no device
+    allocation inside the library (fixed scratch of GPK_NOALLOC_SCRATCH_BYTES)."""
+    import torch
+    fn = lib().gp_kmvm_noalloc
+    fn.restype = _c_int
+    fn.argtypes = [ctypes.POINTER(_Hyp), _c_void_p, _c_i64, _c_void_p, _c_i64, _c_void_p, _c_int, _c_void_p,
+                   _c_int, _c_void_p]
+    Xc = Xr if Xc is None else Xc
+    Nr, d = Xr.shape
+    Nc = Xc.shape[0]
+    R = V.shape[0]
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    fl = prec | int(flags) | (MVM_ADD_NOISE if add_noise else 0)
+    if out is None:
+        out = torch.empty((R, Nr), dtype=torch.float32, device=V.device)
+    h = hyp.c()
+    st = fn(ctypes.byref(h), _dev_ptr(Xr, "Xr", (Nr, d)), Nr, _dev_ptr(Xc, "Xc", (Nc, d)), Nc,
+            _dev_ptr(V, "V", (R, Nc)), R, _dev_ptr(out, "out", (R, Nr)), fl, _stream_ptr(stream))
+    _check(st, "gp_kmvm_noalloc")
+    return out
