@@ -127,6 +127,12 @@ GPK_API int gp_ctx_profile(gp_ctx* ctx, int enable);
 GPK_API int gp_ctx_profile_read(gp_ctx* ctx, double* total_ms, int64_t* launches);
 GPK_API int gp_measure_peaks(gp_ctx* ctx, double* ex2_per_s, double* sqrt_per_s, double* ffma_per_s,
                              void* stream);
+/* As gp_measure_peaks, plus FP32-pair -> FP16x2 pack conversions per second
+ * (round trip, counted once per pair) and kernel values per second of the
+ * FP16 epilogue mix (two ex2 and one pack per pair of values); any output
+ * pointer may be NULL. */
+GPK_API int gp_measure_peaks2(gp_ctx* ctx, double* ex2_per_s, double* sqrt_per_s, double* ffma_per_s,
+                              double* pack_per_s, double* ex2pack_per_s, void* stream);
 
 /* ---- S1+S2: matrix-free kernel MVM (Eq. mvm, Sec. 4.1) --------------------
  *   out[:, c] = a^2 K(Xr, Xc) V[:, c]  (+ sigma^2 V[:, c] with GP_MVM_ADD_NOISE)

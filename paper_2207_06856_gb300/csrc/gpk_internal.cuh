@@ -74,7 +74,7 @@ enum DevErr : int {
     DEV_BREAKDOWN = 3,
 };
 
-// Wait limit for device-side spins (nanoseconds of %globaltimer).
+// Wait limit for device-side spins (nanoseconds; counted in SM clock cycles).
 constexpr uint64_t kWaitLimitNs = 1000000000ull;   // 1 s
 
 // ----------------------------------------------------------------------------

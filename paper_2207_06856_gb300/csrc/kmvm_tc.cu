@@ -9,18 +9,24 @@
 //   2. One thread issues S = XA_i XB_j^T (tcgen05.mma kind::f16, M=N=128,
 //      K = 16/32/64) into a TMEM buffer; with the norm terms folded into the
 //      contraction dimension S is already s_ij = -c^2 r_ij^2 / 2.
-//   3. An epilogue warpgroup reads its S rows from TMEM (one row per
-//      thread), evaluates the kernel function on the special function units,
-//      rounds the tile to FP16/BF16 and writes it back into the same TMEM
-//      columns as P.
+//   3. An epilogue warpgroup loads its whole S tile from TMEM (one row per
+//      thread, 4 loads in flight), releases the S buffer at once so the next
+//      S product can start, evaluates the kernel function on the special
+//      function units, rounds to FP16/BF16 and stores P into its own TMEM
+//      buffer.
 //   4. The MMA thread issues O += P Vt_j^T with P taken from TMEM
 //      (M = 128, N = R_pad, K = 128), accumulating in FP32 in TMEM.  This is
 //      the paper's block summation in higher precision, with 128 x 128 blocks.
-// Two S buffers and two epilogue warpgroups alternate so that the special
-// function units (the roofline of this kernel) stay busy while the tensor
-// core works on the other buffer.  After the last column tile, warpgroup 0
+// Tiles alternate between two epilogue warpgroups and two P buffers; the S
+// product of tile t+2 runs while the epilogue of tile t is still computing,
+// so the special function units (the roofline of this kernel) see no bubble
+// from the tensor-core round trip.  After the last column tile, warpgroup 0
 // reads O and writes a^2 O / s_c (+ sigma^2 v) -- or the raw partial when the
 // column range is split across CTAs -- straight to global memory.
+//
+// TMEM columns: S buffers [0, 128 nsb), P buffers of 64 (hi) or 128 (hi, lo)
+// columns after them, then O (R_pad <= 64).  FP16: 2 S + 2 x 64 P + O = 448;
+// BF16 hi+lo: 1 S + 2 x 128 P + O = 448 (one S buffer, released early).
 //
 // Warp roles (320 threads): warps 0-3 epilogue WG0, 4-7 epilogue WG1,
 // warp 8 TMA producer, warp 9 MMA issuer + TMEM owner.  Persistent CTAs walk
@@ -37,13 +43,12 @@ namespace {
 
 constexpr int kBM = 128;
 constexpr int kBN = 128;
-constexpr int kStages = 4;
+constexpr int kStages = 8;
 constexpr int kThreads = 320;
 constexpr int kTmaWarp = 8;
 constexpr int kMmaWarp = 9;
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kOCol = 256;          // O accumulator columns [256, 256 + R_pad), R_pad <= 64
-constexpr uint32_t kPLoCol = 320;        // lo parts of the kernel tile (split mode): [320 + 64 b, +64)
+
 constexpr int kMinSmemBytes = 120 * 1024; // keeps one CTA per SM (TMEM is taken whole)
 constexpr int kMaxSmemBytes = 227 * 1024; // opt-in maximum per CTA
 
@@ -51,7 +56,7 @@ struct TcParams {
     int n_it, n_jt, n_split, n_items;
     int k_pad, R_pad, R;
     int vsplit;                  // 1: Vt carries hi rows then lo rows
-    int psplit;                  // 1: the kernel tile is carried as hi (in place) + lo (kPLoCol)
+    int psplit;                  // 1: the kernel tile is carried as hi + lo (two P column blocks)
     int stages;                  // shared-memory ring depth (<= kStages)
     int diag;                    // square operator: P_ii is set to 0 on chip and the exact
                                  // a^2 v_i is added with the noise term (k(x, x) = 1)
@@ -72,15 +77,32 @@ struct TcBarriers {
     uint64_t full[kStages];
     uint64_t empty[kStages];
     uint64_t s_full[2];
+    uint64_t s_empty[2];
     uint64_t p_full[2];
+    uint64_t pv_done[2];
     uint64_t o_full;
     uint64_t o_empty;
-    uint64_t xi_full;
-    uint64_t xi_empty;
+    uint64_t xi_full[2];      // row tile of item ic lives in buffer ic & 1
+    uint64_t xi_empty[2];
     uint64_t drain;
 };
 
 __device__ __forceinline__ void record_error(int* err, int code) { atomicCAS(err, 0, code); }
+
+// TMEM column layout (see the header comment).
+struct TmemCols {
+    uint32_t nsb;     // S buffers (2, or 1 with the hi + lo kernel tile)
+    uint32_t pw;      // columns of one P buffer (64 or 128)
+    __device__ __forceinline__ uint32_t s(uint32_t b) const { return b * 128u; }
+    __device__ __forceinline__ uint32_t p(uint32_t b) const { return nsb * 128u + b * pw; }
+    __device__ __forceinline__ uint32_t o() const { return nsb * 128u + 2u * pw; }
+};
+__device__ __forceinline__ TmemCols tmem_cols(int psplit) {
+    TmemCols c;
+    c.nsb = psplit ? 1u : 2u;
+    c.pw = psplit ? 128u : 64u;
+    return c;
+}
 
 __device__ __forceinline__ void item_range(const TcParams& p, int item, int& it, int& j0, int& j1) {
     it = item % p.n_it;
@@ -102,10 +124,12 @@ __device__ void tc_producer(const TcParams& p, const CUtensorMap* tmA, const CUt
     for (int item = blockIdx.x; item < p.n_items; item += gridDim.x, ++ic) {
         int it, j0, j1;
         item_range(p, item, it, j0, j1);
-        if (ic > 0 && !ptx::mbar_wait(&bars.xi_empty, (ic - 1) & 1, p.limit_ns)) { ok = false; break; }
-        ptx::mbar_arrive_expect_tx(&bars.xi_full, xbytes);
+        const int xb = ic & 1;
+        if (ic >= 2 && !ptx::mbar_wait(&bars.xi_empty[xb], ((ic >> 1) - 1) & 1, p.limit_ns)) { ok = false; break; }
+        uint8_t* sX = sXi + xb * xbytes;
+        ptx::mbar_arrive_expect_tx(&bars.xi_full[xb], xbytes);
         for (int a = 0; a < natoms; ++a)
-            ptx::tma_load_2d(sXi + a * abytes, tmA, &bars.xi_full, a * 64, it * kBM);
+            ptx::tma_load_2d(sX + a * abytes, tmA, &bars.xi_full[xb], a * 64, it * kBM);
         ++xi_loads;
         for (int jt = j0; jt < j1; ++jt) {
             const uint32_t st = fills % S, u = fills / S;
@@ -128,11 +152,16 @@ __device__ void tc_producer(const TcParams& p, const CUtensorMap* tmA, const CUt
         // Let every copy this thread issued land before the CTA can exit.
         const uint32_t first = fills > S ? fills - S : 0;
         for (uint32_t f = first; f < fills; ++f) ptx::mbar_wait(&bars.full[f % S], (f / S) & 1, p.limit_ns);
-        if (xi_loads > 0) ptx::mbar_wait(&bars.xi_full, (xi_loads - 1) & 1, p.limit_ns);
+        for (uint32_t q = xi_loads > 2 ? xi_loads - 2 : 0; q < xi_loads; ++q)
+            ptx::mbar_wait(&bars.xi_full[q & 1], (q >> 1) & 1, p.limit_ns);
     }
 }
 
 // ---- MMA issuer (one thread) ----------------------------------------------------
+// Event driven: the thread polls (non-blocking) and issues whichever product
+// is ready -- S(g) into S buffer g % nsb once the epilogue has loaded
+// S(g - nsb) from it and the operands have landed, P.V(g) once P(g) is
+// stored -- so neither kind of product waits behind the other.
 __device__ void tc_mma(const TcParams& p, TcBarriers& bars, const uint8_t* sXi, const uint8_t* sSt,
                        uint32_t xbytes, uint32_t vbytes, uint32_t tmem, uint32_t id_s, uint32_t id_pv) {
     const uint32_t arow = p.k_pad * 2 < 128 ? (uint32_t)p.k_pad * 2u : 128u;  // bytes per row of one atom
@@ -141,9 +170,14 @@ __device__ void tc_mma(const TcParams& p, TcBarriers& bars, const uint8_t* sXi, 
     const uint32_t abytes = (uint32_t)kBM * arow;                            // one atom of a 128-row tile
     const int ksteps = p.k_pad / 16;
     const uint32_t S = (uint32_t)p.stages;
-    const uint32_t aXi = ptx::smem_u32(sXi);
+    const TmemCols tc = tmem_cols(p.psplit);
     const uint32_t aSt = ptx::smem_u32(sSt);
     const uint32_t stage_bytes = xbytes + vbytes;
+    const uint32_t vbox = (uint32_t)p.R_pad * 128u;
+    const int nprod = 1 + p.vsplit + p.psplit;
+    const long long limit = (long long)(p.limit_ns * 2ull);
+    const uint32_t hi_x = ptx::smem_desc_hi(sbo_x, swz);   // row tiles: swizzle by row width
+    const uint32_t hi_v = ptx::smem_desc_hi(1024u, 2u);     // right-hand sides: 128-byte swizzle
     uint32_t n = 0, gt = 0;
     int ic = 0;
     bool ok = true;
@@ -151,62 +185,75 @@ __device__ void tc_mma(const TcParams& p, TcBarriers& bars, const uint8_t* sXi, 
         int it, j0, j1;
         item_range(p, item, it, j0, j1);
         const uint32_t T = (uint32_t)(j1 - j0);
-        if (!ptx::mbar_wait(&bars.xi_full, ic & 1, p.limit_ns)) { ok = false; break; }
-        if (ic > 0 && !ptx::mbar_wait(&bars.o_full, (ic - 1) & 1, p.limit_ns)) { ok = false; break; }
-        // (the previous item's last P.V products are complete: their TMEM
-        //  buffers may now receive this item's first S tiles)
+        const int xb = ic & 1;
+        if (!ptx::mbar_wait(&bars.xi_full[xb], (ic >> 1) & 1, p.limit_ns)) { ok = false; break; }
         ptx::tc_fence_after();
-        auto issue_s = [&](uint32_t t) -> bool {
-            const uint32_t f = n + t, st = f % S;
-            if (!ptx::mbar_wait(&bars.full[st], (f / S) & 1, p.limit_ns)) return false;
-            ptx::tc_fence_after();
-            const uint32_t b = (gt + t) & 1;
-            const uint32_t aXj = aSt + st * stage_bytes;
-            for (int kk = 0; kk < ksteps; ++kk) {
-                const uint32_t koff = ((uint32_t)kk * 32u / arow) * abytes + ((uint32_t)kk * 32u) % arow;
-                const uint64_t da = ptx::smem_desc(aXi + koff, 16, sbo_x, swz);
-                const uint64_t db = ptx::smem_desc(aXj + koff, 16, sbo_x, swz);
-                ptx::mma_f16_ss(tmem + b * 128u, da, db, id_s, kk > 0 ? 1u : 0u);
-            }
-            ptx::mma_commit(&bars.s_full[b]);
-            return true;
-        };
-        if (!issue_s(0)) { ok = false; break; }
-        if (T > 1 && !issue_s(1)) { ok = false; break; }
-        for (uint32_t t = 0; t < T; ++t) {
-            const uint32_t g = gt + t, b = g & 1;
-            if (!ptx::mbar_wait(&bars.p_full[b], (g >> 1) & 1, p.limit_ns)) { ok = false; break; }
-            ptx::tc_fence_after();
-            if (t == 0 && ic > 0) {
-                if (!ptx::mbar_wait(&bars.o_empty, (ic - 1) & 1, p.limit_ns)) { ok = false; break; }
-                ptx::tc_fence_after();
-            }
-            const uint32_t f = n + t, st = f % S;
-            const uint32_t aV = aSt + st * stage_bytes + xbytes;
-            const uint32_t vbox = (uint32_t)p.R_pad * 128u;
-            // Products accumulated into O: P_hi V_hi, then P_hi V_lo (vsplit), then P_lo V_hi (psplit).
-            const int nprod = 1 + p.vsplit + p.psplit;
-            for (int q = 0; q < nprod; ++q) {
-                const uint32_t vpart = (q == 1 && p.vsplit) ? 1u : 0u;
-                const uint32_t pcol = (q == nprod - 1 && p.psplit && q > 0) ? (kPLoCol + b * 64u) : (b * 128u);
-                for (int kk = 0; kk < kBN / 16; ++kk) {
-                    const uint32_t atom = (uint32_t)kk >> 2, kin = (uint32_t)kk & 3u;
-                    const uint64_t dv =
-                        ptx::smem_desc(aV + (2u * vpart + atom) * vbox + kin * 32u, 16, 1024, 2u);
-                    ptx::mma_f16_ts(tmem + kOCol, tmem + pcol + (uint32_t)kk * 8u, dv, id_pv,
-                                    (t > 0 || kk > 0 || q > 0) ? 1u : 0u);
+        const uint32_t aXi = ptx::smem_u32(sXi) + (uint32_t)xb * xbytes;
+        uint32_t ts = 0, tp = 0;            // next tile for S, next tile for P.V
+        long long idle_since = clock64();
+        while (tp < T) {
+            bool progressed = false;
+            // ---- S(ts): needs its S buffer released and its operands landed
+            if (ts < T) {
+                const uint32_t g = gt + ts, b = g % tc.nsb, f = n + ts, st = f % S;
+                const bool buf_free = (g < tc.nsb) || ptx::mbar_test(&bars.s_empty[b], (g / tc.nsb - 1) & 1);
+                if (buf_free && ptx::mbar_test(&bars.full[st], (f / S) & 1)) {
+                    ptx::tc_fence_after();
+                    const uint32_t aXj = aSt + st * stage_bytes;
+                    const uint32_t dS = tmem + tc.s(b);
+                    for (int kk = 0; kk < ksteps; ++kk) {
+                        const uint32_t koff = ((uint32_t)kk * 32u / arow) * abytes + ((uint32_t)kk * 32u) % arow;
+                        ptx::mma_f16_ss(dS, ptx::smem_desc_at(hi_x, aXi + koff), ptx::smem_desc_at(hi_x, aXj + koff),
+                                        id_s, kk > 0 ? 1u : 0u);
+                    }
+                    ptx::mma_commit(&bars.s_full[g & 1]);   // one barrier per epilogue warpgroup
+                    if (ts + 1 == T) ptx::mma_commit(&bars.xi_empty[xb]);   // last use of this row tile
+                    ++ts;
+                    progressed = true;
                 }
             }
-            ptx::mma_commit(&bars.empty[st]);
-            if (t + 2 < T) {
-                // P in buffer b must be consumed before S(t+2) overwrites it.
-                if (!ptx::mbar_wait(&bars.empty[st], (f / S) & 1, p.limit_ns)) { ok = false; break; }
-                if (!issue_s(t + 2)) { ok = false; break; }
+            // ---- P.V(tp): needs P(tp) stored (and, first in an item, O read out)
+            if (tp < ts) {
+                const uint32_t g = gt + tp, pb = g & 1;
+                const bool o_free = (tp > 0) || (ic == 0) || ptx::mbar_test(&bars.o_empty, (ic - 1) & 1);
+                if (o_free && ptx::mbar_test(&bars.p_full[pb], (g >> 1) & 1)) {
+                    ptx::tc_fence_after();
+                    const uint32_t f = n + tp, st = f % S;
+                    const uint32_t aV = aSt + st * stage_bytes + xbytes;
+                    // Products accumulated into O: P_hi V_hi, then P_hi V_lo (vsplit), then P_lo V_hi (psplit).
+                    const uint32_t dO = tmem + tc.o();
+                    for (int q = 0; q < nprod; ++q) {
+                        const uint32_t vpart = (q == 1 && p.vsplit) ? 1u : 0u;
+                        const uint32_t aP = tmem + tc.p(pb) + ((q == nprod - 1 && p.psplit && q > 0) ? 64u : 0u);
+                        const uint32_t aVq = aV + 2u * vpart * vbox;
+                        const uint32_t acc0 = (tp > 0 || q > 0) ? 1u : 0u;
+#pragma unroll
+                        for (int kk = 0; kk < kBN / 16; ++kk) {
+                            const uint32_t off = (uint32_t)(kk >> 2) * vbox + (uint32_t)(kk & 3) * 32u;
+                            ptx::mma_f16_ts(dO, aP + (uint32_t)kk * 8u, ptx::smem_desc_at(hi_v, aVq + off), id_pv,
+                                            kk > 0 ? 1u : acc0);
+                        }
+                    }
+                    ptx::mma_commit(&bars.empty[st]);     // X_j and V_j of this stage are consumed
+                    ptx::mma_commit(&bars.pv_done[pb]);   // P buffer pb may be rewritten
+                    ++tp;
+                    progressed = true;
+                }
+            }
+            if (progressed) {
+                idle_since = clock64();
+            } else {
+                // Back off: this warp shares its scheduler with two epilogue warps,
+                // and a tight poll loop would take their issue slots.
+                __nanosleep(64);
+                if (clock64() - idle_since > limit) {
+                    ok = false;
+                    break;
+                }
             }
         }
         if (!ok) break;
         ptx::mma_commit(&bars.o_full);
-        ptx::mma_commit(&bars.xi_empty);
         n += T;
         gt += T;
     }
@@ -240,9 +287,35 @@ __device__ __forceinline__ float unpack_hi(uint32_t v) {
 }
 
 template <int KIND, int BF16, int PSPLIT>
+__device__ __forceinline__ void tc_chunk(const uint32_t (&r)[32], int h, int row, bool dtile, uint32_t tP,
+                                         uint32_t tPlo) {
+    uint32_t pk[16];
+    uint32_t pl[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        float k0 = kernel_from_s<KIND>(__uint_as_float(r[2 * e]));
+        float k1 = kernel_from_s<KIND>(__uint_as_float(r[2 * e + 1]));
+        if constexpr (KIND == GP_KERNEL_MATERN12) {
+            // exp(-r) has a kink at r = 0: the on-chip diagonal is skipped and the
+            // exact a^2 v_i is added with the noise term instead.
+            if (dtile) {
+                const int col = h * 32 + 2 * e;
+                if (col == row) k0 = 0.0f;
+                if (col + 1 == row) k1 = 0.0f;
+            }
+        }
+        pk[e] = pack2<BF16>(k0, k1);
+        if constexpr (PSPLIT) pl[e] = pack2<BF16>(k0 - unpack_lo<BF16>(pk[e]), k1 - unpack_hi<BF16>(pk[e]));
+    }
+    ptx::tmem_st16(tP + (uint32_t)h * 16u, pk);
+    if constexpr (PSPLIT) ptx::tmem_st16(tPlo + (uint32_t)h * 16u, pl);
+}
+
+template <int KIND, int BF16, int PSPLIT>
 __device__ void tc_epilogue(const TcParams& p, TcBarriers& bars, uint32_t tmem, int wg, int wq, int lane) {
     const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
     const int row = wq * 32 + lane;
+    const TmemCols tc = tmem_cols(PSPLIT);
     uint32_t gt = 0;
     int ic = 0;
     bool ok = true;
@@ -251,37 +324,43 @@ __device__ void tc_epilogue(const TcParams& p, TcBarriers& bars, uint32_t tmem, 
         item_range(p, item, it, j0, j1);
         const uint32_t T = (uint32_t)(j1 - j0);
         for (uint32_t t = 0; t < T; ++t) {
-            const uint32_t g = gt + t, b = g & 1;
-            if ((int)b != wg) continue;
-            if (!ptx::mbar_wait(&bars.s_full[b], (g >> 1) & 1, p.limit_ns)) { ok = false; break; }
+            const uint32_t g = gt + t, pb = g & 1;
+            if ((int)pb != wg) continue;
+            const uint32_t sb = g % tc.nsb;
+            // s_full[pb] completes once per tile of this warpgroup (tiles g = pb, pb + 2, ...),
+            // so a waiter is never more than one phase behind (parity waits stay exact)
+            if (!ptx::mbar_wait(&bars.s_full[pb], (g >> 1) & 1, p.limit_ns)) { ok = false; break; }
             ptx::tc_fence_after();
-            const uint32_t tS = tmem + lane_off + b * 128u;
-            const bool dtile = p.diag && (j0 + (int)t == it);
-#pragma unroll 1
-            for (int h = 0; h < 4; ++h) {
-                uint32_t r[32];
-                ptx::tmem_ld32(tS + (uint32_t)h * 32u, r);
-                ptx::tmem_wait_ld();
-                uint32_t pk[16];
-                uint32_t pl[16];
-#pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    float k0 = kernel_from_s<KIND>(__uint_as_float(r[2 * e]));
-                    float k1 = kernel_from_s<KIND>(__uint_as_float(r[2 * e + 1]));
-                    if (dtile) {
-                        const int col = h * 32 + 2 * e;
-                        if (col == row) k0 = 0.0f;
-                        if (col + 1 == row) k1 = 0.0f;
-                    }
-                    pk[e] = pack2<BF16>(k0, k1);
-                    if constexpr (PSPLIT) pl[e] = pack2<BF16>(k0 - unpack_lo<BF16>(pk[e]), k1 - unpack_hi<BF16>(pk[e]));
-                }
-                ptx::tmem_st16(tS + (uint32_t)h * 16u, pk);
-                if constexpr (PSPLIT) ptx::tmem_st16(tmem + lane_off + kPLoCol + b * 64u + (uint32_t)h * 16u, pl);
+            const uint32_t tS = tmem + lane_off + tc.s(sb);
+            const bool dtile = (KIND == GP_KERNEL_MATERN12) && p.diag && (j0 + (int)t == it);
+            const uint32_t tP = tmem + lane_off + tc.p(pb);
+            const uint32_t tPlo = tP + 64u;
+            // The tile is processed in two 64-column halves (about 110 live registers,
+            // no spills under the 168-register budget of 320 threads).
+            uint32_t ra[32], rb[32];
+            ptx::tmem_ld32(tS, ra);
+            ptx::tmem_ld32(tS + 32u, rb);
+            ptx::tmem_wait_ld();
+            ptx::tmem_reg_fence(ra);
+            ptx::tmem_reg_fence(rb);
+            if (g >= 2) {                            // P.V of the buffer's previous tile is done
+                if (!ptx::mbar_wait(&bars.pv_done[pb], ((g >> 1) - 1) & 1, p.limit_ns)) { ok = false; break; }
+                ptx::tc_fence_after();
             }
+            tc_chunk<KIND, BF16, PSPLIT>(ra, 0, row, dtile, tP, tPlo);
+            tc_chunk<KIND, BF16, PSPLIT>(rb, 1, row, dtile, tP, tPlo);
+            ptx::tmem_ld32(tS + 64u, ra);
+            ptx::tmem_ld32(tS + 96u, rb);
+            ptx::tmem_wait_ld();
+            ptx::tmem_reg_fence(ra);
+            ptx::tmem_reg_fence(rb);
+            ptx::tc_fence_before();
+            ptx::mbar_arrive(&bars.s_empty[sb]);     // the MMA may overwrite this S buffer now
+            tc_chunk<KIND, BF16, PSPLIT>(ra, 2, row, dtile, tP, tPlo);
+            tc_chunk<KIND, BF16, PSPLIT>(rb, 3, row, dtile, tP, tPlo);
             ptx::tmem_wait_st();
             ptx::tc_fence_before();
-            ptx::mbar_arrive(&bars.p_full[b]);
+            ptx::mbar_arrive(&bars.p_full[pb]);
         }
         if (!ok) break;
         if (wg == 0) {
@@ -291,8 +370,9 @@ __device__ void tc_epilogue(const TcParams& p, TcBarriers& bars, uint32_t tmem, 
             const int sp = item / p.n_it;
             for (int c0 = 0; c0 < p.R_pad; c0 += 16) {
                 uint32_t o[16];
-                ptx::tmem_ld16(tmem + lane_off + kOCol + (uint32_t)c0, o);
+                ptx::tmem_ld16(tmem + lane_off + tc.o() + (uint32_t)c0, o);
                 ptx::tmem_wait_ld();
+                ptx::tmem_reg_fence(o);
                 if (i < p.Nr) {
 #pragma unroll
                     for (int e = 0; e < 16; ++e) {
@@ -329,8 +409,8 @@ kmvm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
     const uint32_t xbytes = (uint32_t)kBM * (uint32_t)p.k_pad * 2u;
     const uint32_t vbytes = (uint32_t)(1 + p.vsplit) * (uint32_t)p.R_pad * (uint32_t)kBN * 2u;
-    uint8_t* sXi = base;
-    uint8_t* sSt = base + xbytes;
+    uint8_t* sXi = base;                 // two row-tile buffers
+    uint8_t* sSt = base + 2 * xbytes;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -340,12 +420,16 @@ kmvm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
         for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(&bars.s_full[b], 1);
+            ptx::mbar_init(&bars.s_empty[b], 128);
             ptx::mbar_init(&bars.p_full[b], 128);
+            ptx::mbar_init(&bars.pv_done[b], 1);
         }
         ptx::mbar_init(&bars.o_full, 1);
         ptx::mbar_init(&bars.o_empty, 128);
-        ptx::mbar_init(&bars.xi_full, 1);
-        ptx::mbar_init(&bars.xi_empty, 1);
+        for (int b = 0; b < 2; ++b) {
+            ptx::mbar_init(&bars.xi_full[b], 1);
+            ptx::mbar_init(&bars.xi_empty[b], 1);
+        }
         ptx::mbar_init(&bars.drain, 1);
         ptx::fence_mbar_init();
     }
@@ -394,14 +478,14 @@ int tc_stages(int k_pad, int R_pad, int vsplit) {
     const int xbytes = kBM * k_pad * 2;
     const int vbytes = (1 + vsplit) * R_pad * kBN * 2;
     for (int st = kStages; st >= 2; --st)
-        if (1024 + xbytes + st * (xbytes + vbytes) <= kMaxSmemBytes) return st;
+        if (1024 + 2 * xbytes + st * (xbytes + vbytes) <= kMaxSmemBytes) return st;
     return 0;
 }
 
 int tc_smem_bytes(int k_pad, int R_pad, int vsplit) {
     const int xbytes = kBM * k_pad * 2;
     const int vbytes = (1 + vsplit) * R_pad * kBN * 2;
-    int need = 1024 + xbytes + tc_stages(k_pad, R_pad, vsplit) * (xbytes + vbytes);
+    int need = 1024 + 2 * xbytes + tc_stages(k_pad, R_pad, vsplit) * (xbytes + vbytes);
     return need < kMinSmemBytes ? kMinSmemBytes : need;
 }
 

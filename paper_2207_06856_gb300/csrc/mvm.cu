@@ -171,7 +171,9 @@ int kop_apply(Ctx* ctx, KOp& op, const float* V, int R, float* out, int64_t ld_o
         a.Vnoise = V + (int64_t)c0 * op.Nc;
         a.out = out + (int64_t)c0 * ld_out;
         a.ld_out = ld_out;
-        a.diag_coef = (op.square && op.prec != GP_PREC_FP32) ? op.a2 : 0.0f;
+        // exp(-r) (Matern-1/2) is not smooth at r = 0, where the rounding of the
+        // on-chip distance would show; its diagonal is added exactly instead.
+        a.diag_coef = (op.square && op.prec != GP_PREC_FP32 && op.kernel == GP_KERNEL_MATERN12) ? op.a2 : 0.0f;
         const float* Vc = V + (int64_t)c0 * op.Nc;
         if (op.prec == GP_PREC_FP32) {
             SimtPlan pl = op.sp;

@@ -21,7 +21,28 @@ __global__ void __launch_bounds__(256) peak_kernel(float seed, float* sink) {
         for (int c = 0; c < kChains; ++c) {
             if constexpr (OP == 0) v[c] = ptx::ex2(-v[c]);              // stays in (0.5, 1)
             else if constexpr (OP == 1) v[c] = ptx::sqrt_approx(v[c] + 0.25f) ;
-            else v[c] = fmaf(v[c], 0.999f, 0.0005f);
+            else if constexpr (OP == 2) v[c] = fmaf(v[c], 0.999f, 0.0005f);
+        }
+        if constexpr (OP == 3) {
+            // FP32 pair -> packed FP16x2 and back (one conversion each way per pair)
+#pragma unroll
+            for (int c = 0; c < kChains; c += 2) {
+                __half2 h = __floats2half2_rn(v[c], v[c + 1]);
+                float2 f = __half22float2(h);
+                v[c] = f.x * 0.999f;
+                v[c + 1] = f.y * 0.999f;
+            }
+        }
+        if constexpr (OP == 4) {
+            // the FP16 epilogue per pair of kernel values: 2 ex2 + 1 pack
+#pragma unroll
+            for (int c = 0; c < kChains; c += 2) {
+                const float a = ptx::ex2(-v[c]), b = ptx::ex2(-v[c + 1]);
+                __half2 h = __floats2half2_rn(a, b);
+                unsigned u = *reinterpret_cast<unsigned*>(&h);
+                v[c] = __uint_as_float((u & 0x3ff) | 0x3f000000u);
+                v[c + 1] = __uint_as_float(((u >> 16) & 0x3ff) | 0x3f000000u);
+            }
         }
     }
     float acc = 0.0f;
@@ -71,6 +92,11 @@ void prof_end(Ctx* ctx, cudaStream_t s) {
 extern "C" {
 
 int gp_measure_peaks(gp_ctx* ctx, double* ex2_per_s, double* sqrt_per_s, double* ffma_per_s, void* stream) {
+    return gp_measure_peaks2(ctx, ex2_per_s, sqrt_per_s, ffma_per_s, nullptr, nullptr, stream);
+}
+
+int gp_measure_peaks2(gp_ctx* ctx, double* ex2_per_s, double* sqrt_per_s, double* ffma_per_s, double* pack_per_s,
+                      double* ex2pack_per_s, void* stream) {
     if (!ctx) return GP_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     float* sink = nullptr;
@@ -78,11 +104,15 @@ int gp_measure_peaks(gp_ctx* ctx, double* ex2_per_s, double* sqrt_per_s, double*
     const double e = gpk::time_peak<0>(ctx, sink, s);
     const double q = gpk::time_peak<1>(ctx, sink, s);
     const double f = gpk::time_peak<2>(ctx, sink, s);
+    const double k = gpk::time_peak<3>(ctx, sink, s);   // counted per chain element: one pair = 2
+    const double m = gpk::time_peak<4>(ctx, sink, s);   // kernel values per second (ex2 + half a pack each)
     cudaFree(sink);
     if (cudaGetLastError() != cudaSuccess) return GP_ERR_CUDA;
     if (ex2_per_s) *ex2_per_s = e;
     if (sqrt_per_s) *sqrt_per_s = q;
     if (ffma_per_s) *ffma_per_s = f;
+    if (pack_per_s) *pack_per_s = k / 2.0;
+    if (ex2pack_per_s) *ex2pack_per_s = m;
     return GP_OK;
 }
 

@@ -1,6 +1,6 @@
 // Inline-PTX wrappers for sm_103a: mbarrier, TMA (cp.async.bulk.tensor),
 // tcgen05 (TMEM allocation, MMA, loads/stores, fences) and special-function
-// unit instructions.  Every wait here is bounded by %globaltimer.
+// unit instructions.  Every mbarrier wait here is bounded (clock64 budget).
 #pragma once
 #include <cuda.h>
 #include <stdint.h>
@@ -46,15 +46,28 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// Non-blocking probe of the phase with the given parity.
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 // Wait for the completion of the phase with the given parity; false after
-// `limit_ns` nanoseconds without completion.
+// about `limit_ns` nanoseconds without completion (SM clock cycles counted at
+// a nominal 2 cycles per ns: a limit, not a measurement).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = globaltimer();
-    uint32_t n = 0;
+    const long long t0 = clock64();
+    const long long lim = (long long)(limit_ns * 2ull);
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((++n & 63u) == 0 && globaltimer() - t0 > limit_ns) return false;
+        if (clock64() - t0 > lim) return false;
     }
 }
 
@@ -129,6 +142,15 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo_bytes
     d |= (uint64_t)(swizzle_code & 7u) << 61;
     return d;
 }
+// The same descriptor split into a constant high word and a low word that
+// only depends on the start address: lo = (addr >> 4) | (lbo >> 4) << 16.
+__device__ __forceinline__ uint32_t smem_desc_hi(uint32_t sbo_bytes, uint32_t swizzle_code) {
+    return ((sbo_bytes >> 4) & 0x3FFFu) | (1u << 14) | ((swizzle_code & 7u) << 29);
+}
+__device__ __forceinline__ uint64_t smem_desc_at(uint32_t hi, uint32_t saddr) {
+    const uint32_t lo = ((saddr & 0x3FFFFu) >> 4) | (1u << 16);   // LBO = 16 bytes (unused for K-major swizzled)
+    return ((uint64_t)hi << 32) | lo;
+}
 // Instruction descriptor for kind::f16 with FP32 accumulation, K-major A and B.
 // a_bf16/b_bf16: 0 = FP16, 1 = BF16.
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N, int bf16) {
@@ -162,6 +184,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// Registers written by tcgen05.ld are valid only after tcgen05.wait::ld.  The
+// outputs of the load asm carry no dependence on the wait asm, so pass each
+// register through an empty volatile asm placed after the wait: volatile asm
+// statements keep their order, so every consumer now follows the wait.
+template <int N>
+__device__ __forceinline__ void tmem_reg_fence(uint32_t (&r)[N]) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) asm volatile("" : "+r"(r[i]));
+}
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
     asm volatile(
         "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "

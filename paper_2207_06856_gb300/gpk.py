@@ -105,6 +105,7 @@ def _declare(lib):
         "gp_ctx_profile_read": (_c_int, [_c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_c_i64)]),
         "gp_measure_peaks": (_c_int, [_c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double), _c_void_p]),
+        "gp_measure_peaks2": (_c_int, [_c_void_p] + [ctypes.POINTER(ctypes.c_double)] * 5 + [_c_void_p]),
         "gp_pivchol_workspace_size": (_c_size, [ctypes.POINTER(_Hyp), _c_i64, _c_int]),
         "gp_pivchol_precond": (_c_int, [_c_void_p, ctypes.POINTER(_Hyp), _c_void_p, _c_i64, _c_int, _c_void_p,
                                         _c_void_p, _c_void_p, ctypes.POINTER(_c_int), _c_void_p]),
@@ -233,10 +234,11 @@ class Context:
 
     def measure_peaks(self, stream=None) -> dict:
         """Measured throughput (ops/s) of ex2, sqrt (special function units) and FP32 FMA."""
-        e, q, f = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
-        _check(lib().gp_measure_peaks(self._p, ctypes.byref(e), ctypes.byref(q), ctypes.byref(f),
-                                      _stream_ptr(stream)), "gp_measure_peaks")
-        return {"ex2_per_s": e.value, "sqrt_per_s": q.value, "ffma_per_s": f.value}
+        e, q, f, k, m = (ctypes.c_double() for _ in range(5))
+        _check(lib().gp_measure_peaks2(self._p, ctypes.byref(e), ctypes.byref(q), ctypes.byref(f), ctypes.byref(k),
+                                       ctypes.byref(m), _stream_ptr(stream)), "gp_measure_peaks2")
+        return {"ex2_per_s": e.value, "sqrt_per_s": q.value, "ffma_per_s": f.value,
+                "pack_f16x2_per_s": k.value, "fp16_epilogue_values_per_s": m.value}
 
 
 def kmvm_workspace_size(hyp: Hyper, Nr: int, Nc: int, R: int, flags: int) -> int:
