@@ -244,6 +244,8 @@ typedef struct {
     double* beta;        /* [max_iter * R]: beta_{k+1} of column c at k*R + c */
     double* gamma0;      /* [R] r_0^T z_0                                     */
     double* resid_hist;  /* [(max_iter + 1) * R] relative residual per iterate */
+    int* lanczos_len;    /* [R] iterations before the first true-residual restart: the
+                            length of the Lanczos process the step sizes describe     */
 } gp_cg_stats_t;
 
 /* Solve (K + sigma^2 I) U = B for R right-hand sides at once (Eq. cg; mBCG of
@@ -261,6 +263,51 @@ GPK_API size_t gp_cg_workspace_size(const gp_hyp_t* hyp, int64_t N, int R, int r
 GPK_API int gp_cg_solve(gp_ctx* ctx, const gp_hyp_t* hyp, const float* X, int64_t N, const float* B, int R,
                         float* U, const gp_precond_t* precond, const gp_cg_opts_t* opts, gp_cg_stats_t* stats,
                         void* stream);
+
+/* ---- S7: backward of the kernel MVM (gradient of a bilinear form) ----------
+ * grad_theta[0..d+2) = d/d(l_1..l_d, a^2, sigma^2) of  q = sum_c u_c^T Ktilde w_c,
+ * and, when grad_X is not NULL, grad_X = dq/dX (device, N x d row-major).
+ * With r^2 = sum_m (x_im - x_jm)^2 / l_m^2 and G_ij = sum_c u_ic w_jc:
+ *   dq/da^2 = sum_ij G_ij k(r^2);  dq/dl_m = -(2/l_m^3) sum_ij G_ij a^2 k'(r^2) (x_im - x_jm)^2;
+ *   dq/dsigma^2 = sum_c u_c^T w_c;  dq/dx_im = (2/l_m^2) sum_j (G_ij + G_ji) a^2 k' (x_im - x_jm).
+ * Pairs are evaluated on the fly in FP32 (CUDA cores), sums reduced in FP64.
+ *   X device N x d; U, W device N x R column-major, 1 <= R <= 32; d <= 32.
+ * grad_theta is host memory; the call synchronises the stream. */
+GPK_API size_t gp_kmvm_vjp_workspace_size(const gp_hyp_t* hyp, int64_t N, int R);
+GPK_API int gp_kmvm_vjp(gp_ctx* ctx, const gp_hyp_t* hyp, const float* X, int64_t N, const float* U,
+                        const float* W, int R, double* grad_theta, float* grad_X, void* stream);
+
+/* ---- S7: stochastic Lanczos quadrature from CG step sizes (host) -----------
+ * out = gamma0 * e1^T log(T) e1 for the Lanczos tridiagonal T of a CG run
+ * with step sizes alpha[0..J) and beta[0..J-1) (beta[k] = beta_{k+1} of
+ * Alg. 2): T_kk = 1/alpha_k + beta_k/alpha_{k-1}, T_{k,k+1} = sqrt(beta_{k+1})/alpha_k.
+ * gamma0 = r_0^T z_0 of that run.  Host only (no GPU needed).  FP64
+ * eigen-decomposition of T by implicit-shift QL. */
+GPK_API int gp_slq_quadrature(const double* alpha, const double* beta, int J, double gamma0, double* out);
+
+/* ---- S7: loss and gradient (Sec. 4.3, Eq. loss / approx_loss / approx) ------ */
+#define GP_MLL_PRECOND_PROBES 0x1  /* z_j = L e_j + sigma z~_j (E[zz^T] = P) from the
+                                      standard normals Z (z~) and E; gradient pairs
+                                      u_j with P^{-1} z_j; enables the SLQ log|Ktilde|
+                                      with log|P| added exactly                       */
+#define GP_MLL_WANT_LOGDET    0x2  /* estimate log|Ktilde| by SLQ for the loss value
+                                      (needs PRECOND_PROBES, or no preconditioner)     */
+/* Solves Ktilde [u_0 .. u_M] = [y, z_1 .. z_M] with gp_cg_solve's method, then
+ *   grad[0..d+2) = gradient of 1/(2M) sum_j u_j^T (dKtilde w_j) - 1/2 u_0^T (dKtilde u_0)
+ *                  w.r.t. (l_1..l_d, a^2, sigma^2)  (Eq. approx; host),
+ *   grad_X       = the same w.r.t. X (device N x d, optional),
+ *   mll          = 1/2 log|Ktilde| + 1/2 y^T u_0 + N/2 log 2 pi  (host, NaN when no
+ *                  log-determinant was requested or it cannot be estimated),
+ *   U            = the solutions (device N x (M+1), optional).
+ *   Z  device, M x N (row j = probe j): Rademacher / Gaussian probes, or the
+ *      standard normals z~ with GP_MLL_PRECOND_PROBES
+ *   E  device, M x rank standard normals (GP_MLL_PRECOND_PROBES only)
+ *   1 <= M <= 31, d <= 32.  Synchronises the stream. */
+GPK_API size_t gp_mll_workspace_size(const gp_hyp_t* hyp, int64_t N, int M, int rank, const gp_cg_opts_t* opts);
+GPK_API int gp_mll_and_grad(gp_ctx* ctx, const gp_hyp_t* hyp, const float* X, const float* y, int64_t N,
+                            const float* Z, int M, const float* E, const gp_precond_t* precond,
+                            const gp_cg_opts_t* opts, int flags, double* mll, double* grad, float* grad_X,
+                            float* U, gp_cg_stats_t* stats, void* stream);
 
 #ifdef __cplusplus
 }

@@ -492,6 +492,7 @@ int cg_run(Ctx* ctx, WsCarver& wc, const gp_hyp_t* hyp, const float* X, int64_t 
     GPK_TRY(start(o->x0_given != 0, 0));
     int n_active = ctx->host_pinned[0];
     int iters = 0, restarts = 0, nb0 = 0;   // nb0: first iteration of the current basis
+    bool first_recorded = false;
 
     int k = 0;
     while (true) {
@@ -528,6 +529,19 @@ int cg_run(Ctx* ctx, WsCarver& wc, const gp_hyp_t* hyp, const float* X, int64_t 
             if (cudaStreamSynchronize(s) != cudaSuccess) return GP_ERR_CUDA;
             n_active = ctx->host_pinned[0];
             iters = k + 1;
+        }
+        if (restarts == 0 && stats && stats->lanczos_len) {
+            // lengths of the first (unrestarted) run: the Lanczos process its step sizes describe
+            ColState* tmp = (ColState*)malloc(sizeof(ColState) * R);
+            if (!tmp) return GP_ERR_OOM;
+            if (cudaMemcpyAsync(tmp, b.st, sizeof(ColState) * R, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess) {
+                free(tmp);
+                return GP_ERR_CUDA;
+            }
+            for (int c = 0; c < R; ++c) stats->lanczos_len[c] = tmp[c].iters;
+            free(tmp);
+            first_recorded = true;
         }
         if (restarts >= o->restarts || k >= o->max_iter) break;
         // True-residual check: recompute r = K x - b; columns above tol restart.
@@ -567,6 +581,7 @@ int cg_run(Ctx* ctx, WsCarver& wc, const gp_hyp_t* hyp, const float* X, int64_t 
         stats->breakdowns = brk;
         stats->restarts = restarts;
         for (int c = 0; c < R; ++c) {
+            if (stats->lanczos_len && !first_recorded) stats->lanczos_len[c] = hs[c].iters;
             if (stats->col_iters) stats->col_iters[c] = hs[c].iters;
             if (stats->rel_resid) stats->rel_resid[c] = hs[c].relres;
             if (stats->gamma0) stats->gamma0[c] = hs[c].gamma0;

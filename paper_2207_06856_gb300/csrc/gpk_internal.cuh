@@ -200,6 +200,17 @@ size_t woodbury_workspace(const Ctx* ctx, int64_t N, int k, int R);
 int woodbury_apply(Ctx* ctx, WsCarver& wc, const float* L, const double* core, int k, double noise, int64_t N,
                    const float* W, int R, const int* active, float* Z, cudaStream_t s);
 
+// ---- solver (cg.cu), backward (vjp.cu), loss (mll.cu) ----
+size_t cg_workspace(const Ctx* ctx, const gp_hyp_t* hyp, int64_t N, int R, int rank, const gp_cg_opts_t* o);
+int cg_run(Ctx* ctx, WsCarver& wc, const gp_hyp_t* hyp, const float* X, int64_t N, const float* B, int R,
+           float* U, const gp_precond_t* pc, const gp_cg_opts_t* o, gp_cg_stats_t* stats, cudaStream_t s);
+size_t vjp_workspace(int64_t N, int d, int R);
+int vjp_run(Ctx* ctx, WsCarver& wc, const gp_hyp_t* hyp, const float* X, int64_t N, const float* U, const float* W,
+            int R, double* grad_theta_host, float* gX_dev, cudaStream_t s);
+int launch_scale_cols(Ctx* ctx, const float* src, int64_t N, int dp, int d, const float* ls_host, float* dst,
+                      cudaStream_t s);
+int slq_quadrature_host(const double* alpha, const double* beta, int J, double gamma0, double* out);
+
 }  // namespace gpk
 
 // The opaque handle of the C ABI is the context itself.

@@ -73,7 +73,8 @@ class _CgStats(ctypes.Structure):
                 ("restarts", ctypes.c_int),
                 ("col_iters", ctypes.POINTER(ctypes.c_int)), ("rel_resid", ctypes.POINTER(ctypes.c_double)),
                 ("alpha", ctypes.POINTER(ctypes.c_double)), ("beta", ctypes.POINTER(ctypes.c_double)),
-                ("gamma0", ctypes.POINTER(ctypes.c_double)), ("resid_hist", ctypes.POINTER(ctypes.c_double))]
+                ("gamma0", ctypes.POINTER(ctypes.c_double)), ("resid_hist", ctypes.POINTER(ctypes.c_double)),
+                ("lanczos_len", ctypes.POINTER(ctypes.c_int))]
 
 
 class _Hyp(ctypes.Structure):
@@ -106,6 +107,16 @@ def _declare(lib):
         "gp_measure_peaks": (_c_int, [_c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double), _c_void_p]),
         "gp_measure_peaks2": (_c_int, [_c_void_p] + [ctypes.POINTER(ctypes.c_double)] * 5 + [_c_void_p]),
+        "gp_kmvm_vjp_workspace_size": (_c_size, [ctypes.POINTER(_Hyp), _c_i64, _c_int]),
+        "gp_kmvm_vjp": (_c_int, [_c_void_p, ctypes.POINTER(_Hyp), _c_void_p, _c_i64, _c_void_p, _c_void_p, _c_int,
+                                 ctypes.POINTER(ctypes.c_double), _c_void_p, _c_void_p]),
+        "gp_slq_quadrature": (_c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _c_int,
+                                       ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
+        "gp_mll_workspace_size": (_c_size, [ctypes.POINTER(_Hyp), _c_i64, _c_int, _c_int, ctypes.POINTER(_CgOpts)]),
+        "gp_mll_and_grad": (_c_int, [_c_void_p, ctypes.POINTER(_Hyp), _c_void_p, _c_void_p, _c_i64, _c_void_p, _c_int,
+                                     _c_void_p, ctypes.POINTER(_Precond), ctypes.POINTER(_CgOpts), _c_int,
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _c_void_p,
+                                     _c_void_p, ctypes.POINTER(_CgStats), _c_void_p]),
         "gp_pivchol_workspace_size": (_c_size, [ctypes.POINTER(_Hyp), _c_i64, _c_int]),
         "gp_pivchol_precond": (_c_int, [_c_void_p, ctypes.POINTER(_Hyp), _c_void_p, _c_i64, _c_int, _c_void_p,
                                         _c_void_p, _c_void_p, ctypes.POINTER(_c_int), _c_void_p]),
@@ -340,9 +351,11 @@ def cg_solve(ctx: Context, hyp: Hyper, X, B, precond: Precond | None = None, tol
     g0 = np.zeros(R, np.float64)
     rh = np.zeros((max_iter + 1) * R, np.float64)
     P = ctypes.POINTER
+    lz = np.zeros(R, np.int32)
     stats = _CgStats(0, 0, 0, 0, col_iters.ctypes.data_as(P(ctypes.c_int)), rel.ctypes.data_as(P(ctypes.c_double)),
                      al.ctypes.data_as(P(ctypes.c_double)), be.ctypes.data_as(P(ctypes.c_double)),
-                     g0.ctypes.data_as(P(ctypes.c_double)), rh.ctypes.data_as(P(ctypes.c_double)))
+                     g0.ctypes.data_as(P(ctypes.c_double)), rh.ctypes.data_as(P(ctypes.c_double)),
+                     lz.ctypes.data_as(P(ctypes.c_int)))
     pc = precond.c() if precond is not None else _Precond(None, None, 0)
     st = lib().gp_cg_solve(ctx.ptr, ctypes.byref(h), _dev_ptr(X, "X", (N, d)), N, _dev_ptr(B, "B", (R, N)), R,
                            _dev_ptr(U, "U", (R, N)), ctypes.byref(pc), ctypes.byref(opts), ctypes.byref(stats),
@@ -354,7 +367,7 @@ def cg_solve(ctx: Context, hyp: Hyper, X, B, precond: Precond | None = None, tol
             "restarts": int(stats.restarts),
             "col_iters": col_iters, "rel_resid": rel, "gamma0": g0,
             "alpha": al.reshape(max_iter, R)[:it], "beta": be.reshape(max_iter, R)[:it],
-            "resid_hist": rh.reshape(max_iter + 1, R)[:it + 1]}
+            "resid_hist": rh.reshape(max_iter + 1, R)[:it + 1], "lanczos_len": lz}
     return U, st, info
 
 
@@ -379,3 +392,85 @@ def kmvm_noalloc(hyp: Hyper, Xr, V, Xc=None, precision="fp16", add_noise=False, 
             _dev_ptr(V, "V", (R, Nc)), R, _dev_ptr(out, "out", (R, Nr)), fl, _stream_ptr(stream))
     _check(st, "gp_kmvm_noalloc")
     return out
+
+
+MLL_PRECOND_PROBES = 0x1
+MLL_WANT_LOGDET = 0x2
+
+
+def kmvm_vjp(ctx: Context, hyp: Hyper, X, U, W, want_X: bool = False, stream=None):
+    """gp_kmvm_vjp: gradient of sum_c u_c^T Ktilde w_c w.r.t. (l_1..l_d, a^2, sigma^2)
+    (numpy, d + 2) and optionally X (CUDA tensor N x d).  U, W: (R, N)."""
+    import torch
+    N, d = X.shape
+    R = U.shape[0]
+    h = hyp.c()
+    need = int(lib().gp_kmvm_vjp_workspace_size(ctypes.byref(h), N, R))
+    if need == 0:
+        raise GPKError(GP_ERR_INVALID, "gp_kmvm_vjp_workspace_size")
+    if need > ctx.workspace_bytes:
+        ctx.reserve(need)
+    g = np.zeros(d + 2, np.float64)
+    gX = torch.empty((N, d), dtype=torch.float32, device=X.device) if want_X else None
+    st = lib().gp_kmvm_vjp(ctx.ptr, ctypes.byref(h), _dev_ptr(X, "X", (N, d)), N, _dev_ptr(U, "U", (R, N)),
+                           _dev_ptr(W, "W", (R, N)), R, g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                           int(gX.data_ptr()) if gX is not None else None, _stream_ptr(stream))
+    _check(st, "gp_kmvm_vjp")
+    return g, gX
+
+
+def slq_quadrature(alpha, beta, gamma0: float) -> float:
+    """gp_slq_quadrature (host only): gamma0 * e1^T log(T) e1 for the Lanczos
+    tridiagonal of CG step sizes alpha[0..J), beta[0..J-1)."""
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    b = np.ascontiguousarray(beta if len(beta) else [0.0], dtype=np.float64)
+    out = ctypes.c_double(0.0)
+    P = ctypes.POINTER(ctypes.c_double)
+    _check(lib().gp_slq_quadrature(a.ctypes.data_as(P), b.ctypes.data_as(P), int(a.shape[0]), float(gamma0),
+                                   ctypes.byref(out)), "gp_slq_quadrature")
+    return float(out.value)
+
+
+def mll_and_grad(ctx: Context, hyp: Hyper, X, y, Z, precond: Precond | None = None, E=None,
+                 precond_probes: bool = False, want_logdet: bool = True, tol: float = 1e-2, max_iter: int = 100,
+                 precision="fp16", want_X: bool = False, return_U: bool = False, restarts: int = 4,
+                 check_precision="fp32", stream=None):
+    """gp_mll_and_grad.  X (N, d), y (N,), Z (M, N) probes [, E (M, rank) normals]
+    -> (mll, grad (numpy, d + 2), grad_X or None, U or None, info)."""
+    import torch
+    N, d = X.shape
+    M = Z.shape[0]
+    R = M + 1
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    opts = _CgOpts(float(tol), int(max_iter), 0, prec, CG_STABLE, REORTH_PINV, 1, 0, int(restarts),
+                   PRECISIONS[check_precision] if isinstance(check_precision, str) else int(check_precision))
+    h = hyp.c()
+    rank = precond.rank if precond is not None else 0
+    need = int(lib().gp_mll_workspace_size(ctypes.byref(h), N, M, rank, ctypes.byref(opts)))
+    if need == 0:
+        raise GPKError(GP_ERR_INVALID, "gp_mll_workspace_size")
+    if need > ctx.workspace_bytes:
+        ctx.reserve(need)
+    flags = (MLL_PRECOND_PROBES if precond_probes else 0) | (MLL_WANT_LOGDET if want_logdet else 0)
+    mll = ctypes.c_double(0.0)
+    g = np.zeros(d + 2, np.float64)
+    gX = torch.empty((N, d), dtype=torch.float32, device=X.device) if want_X else None
+    U = torch.empty((R, N), dtype=torch.float32, device=X.device) if return_U else None
+    col_iters = np.zeros(R, np.int32)
+    rel = np.zeros(R, np.float64)
+    g0 = np.zeros(R, np.float64)
+    lz = np.zeros(R, np.int32)
+    Pd, Pi = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+    stats = _CgStats(0, 0, 0, 0, col_iters.ctypes.data_as(Pi), rel.ctypes.data_as(Pd), None, None,
+                     g0.ctypes.data_as(Pd), None, lz.ctypes.data_as(Pi))
+    pc = precond.c() if precond is not None else _Precond(None, None, 0)
+    st = lib().gp_mll_and_grad(ctx.ptr, ctypes.byref(h), _dev_ptr(X, "X", (N, d)), _dev_ptr(y, "y", (N,)), N,
+                               _dev_ptr(Z, "Z", (M, N)), M,
+                               _dev_ptr(E, "E", (M, rank)) if E is not None else None,
+                               ctypes.byref(pc), ctypes.byref(opts), flags, ctypes.byref(mll),
+                               g.ctypes.data_as(Pd), int(gX.data_ptr()) if gX is not None else None,
+                               int(U.data_ptr()) if U is not None else None, ctypes.byref(stats), _stream_ptr(stream))
+    _check(st, "gp_mll_and_grad")
+    info = {"iters": int(stats.iters), "converged": int(stats.converged), "restarts": int(stats.restarts),
+            "col_iters": col_iters, "rel_resid": rel, "gamma0": g0, "lanczos_len": lz}
+    return float(mll.value), g, gX, U, info

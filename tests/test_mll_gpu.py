@@ -1,0 +1,130 @@
+"""Backward of the kernel MVM (gp_kmvm_vjp) and the loss / gradient
+(gp_mll_and_grad, Eq. loss / approx) against the FP64 oracle.
+
+Tolerances: the FP32 backward against the FP64 bilinear-form gradient 1e-4
+(relative, vector norm); gradients from solves <= 1e-2 relative against the
+same-probe FP64 estimator (exact solves); the loss value <= 1e-3 relative
+against the same-probe FP64 SLQ estimate."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2207_06856_gb300 import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+KNAME = {0: "rbf", 1: "matern32", 2: "matern12", 3: "matern52"}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2207_06856_gb300 import gpk
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = gpk.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to("cuda:0")
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+@pytest.mark.parametrize("kern", [0, 1, 2, 3])
+@pytest.mark.parametrize("shape", [(300, 3, 2), (1000, 8, 17), (777, 18, 5)])
+def test_vjp_matches_oracle(ctx, kern, shape):
+    from paper_2207_06856_gb300 import gpk
+    N, d, R = shape
+    X, V, _, ls, a2, s2 = workloads.random_problem(N, d, R, seed=N + d, kernel=kern)
+    U = np.random.default_rng(N).standard_normal((R, N)).astype(np.float32)
+    hyp = gpk.Hyper(kern, ls, a2, s2)
+    g, gX = gpk.kmvm_vjp(ctx, hyp, _dev(X), _dev(U), _dev(V), want_X=True)
+    ref, refX = O.quad_form_grad(X, O.Hyp(KNAME[kern], ls, a2, s2), U.T, V.T, wrt_X=True)
+    assert _rel(g, ref) <= 1e-4, (g, ref)
+    assert _rel(gX.cpu().numpy(), refX) <= 1e-4
+
+
+def _problem(N=1500, d=5, M=8, seed=3, kernel=0):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((N, d)).astype(np.float32)
+    y = (np.sin(X.sum(axis=1)) + 0.1 * rng.standard_normal(N)).astype(np.float32)
+    ls = np.full(d, 1.2, np.float32)
+    return X, y, ls, 1.1, 0.05, M, kernel
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-6), ("fp16", 1e-3)])
+def test_gradient_matches_same_probe_estimator(ctx, prec, tol):
+    """Rademacher probes (E[zz^T] = I), no preconditioner: the library's
+    gradient against Eq. approx evaluated in FP64 with exact solves."""
+    from paper_2207_06856_gb300 import gpk
+    X, y, ls, a2, s2, M, kern = _problem()
+    Z = workloads.rademacher(np.random.default_rng(9), M, X.shape[0])
+    hyp = gpk.Hyper(kern, ls, a2, s2)
+    mll, g, _, U, info = gpk.mll_and_grad(ctx, hyp, _dev(X), _dev(y), _dev(Z), tol=tol, max_iter=500,
+                                          precision=prec, want_logdet=True, return_U=True)
+    oh = O.Hyp("rbf", ls, a2, s2)
+    B = np.column_stack([y, Z.T]).astype(np.float64)
+    Uex = O.cholesky_solve(X, oh, B)
+    ref = O.pseudo_loss_grad(X, oh, Uex, Z.T.astype(np.float64))
+    assert _rel(g, ref) <= 1e-2, (g, ref)
+    # the same-probe estimator approximates the exact gradient (Hutchinson variance)
+    exact = O.mll_grad_exact(X, y, oh)
+    assert _rel(ref, exact) < 0.5
+
+
+def test_mll_value_with_preconditioner_probes(ctx):
+    """P-distributed probes z = L e + sigma z~, SLQ log-determinant plus log|P|:
+    the loss against the same-probe FP64 SLQ estimate (1e-3) and the exact
+    loss (within the estimator's spread)."""
+    from paper_2207_06856_gb300 import gpk
+    X, y, ls, a2, s2, M, kern = _problem(N=1200, M=16, seed=4)
+    rank = 20
+    rng = np.random.default_rng(11)
+    Zt = rng.standard_normal((M, X.shape[0])).astype(np.float32)
+    E = rng.standard_normal((M, rank)).astype(np.float32)
+    hyp = gpk.Hyper(kern, ls, a2, s2)
+    Xd = _dev(X)
+    pc = gpk.pivchol(ctx, hyp, Xd, rank)
+    mll, g, _, U, info = gpk.mll_and_grad(ctx, hyp, Xd, _dev(y), _dev(Zt), precond=pc, E=_dev(E),
+                                          precond_probes=True, want_logdet=True, tol=1e-6, max_iter=400,
+                                          precision="fp32", return_U=True, restarts=0)
+    oh = O.Hyp("rbf", ls, a2, s2)
+    # the oracle builds the same probes from the GPU's L (FP32 factor, pivots as chosen)
+    L = pc.L.cpu().numpy().astype(np.float64).T
+    Zp = (L @ E.T.astype(np.float64) + math.sqrt(s2) * Zt.T.astype(np.float64))   # N x M
+    Kt = O.ktilde_dense(X, oh)
+    pre = lambda r: O.precond_apply(L, s2, r)  # noqa: E731
+    est = []
+    for j in range(M):
+        res = O.cg_stable(lambda v: Kt @ v, Zp[:, j], precond=pre, tol=1e-10, max_iter=X.shape[0])
+        est.append(O.slq_quadrature(O.lanczos_tridiagonal(res.alphas, res.betas), res.gamma0))
+    logdet_slq = O.precond_logdet(L, s2) + float(np.mean(est))
+    alpha = np.linalg.solve(Kt, y.astype(np.float64))
+    ref = 0.5 * logdet_slq + 0.5 * float(y @ alpha) + 0.5 * X.shape[0] * math.log(2 * math.pi)
+    assert abs(mll - ref) <= 1e-3 * abs(ref), (mll, ref)
+    exact = O.mll_exact(X, y, oh)
+    spread = 0.5 * float(np.std(est)) / math.sqrt(M)
+    assert abs(mll - exact) <= 5 * spread + 1e-3 * abs(exact), (mll, exact, spread)
+    # gradient with P-probes against the same-probe FP64 estimator (u_j paired with P^{-1} z_j)
+    B = np.column_stack([y.astype(np.float64), Zp])
+    Uex = np.linalg.solve(Kt, B)
+    refg = O.pseudo_loss_grad(X, oh, Uex, Zp, W=pre(Zp))
+    assert _rel(g, refg) <= 1e-2, (g, refg)
+
+
+def test_autograd_fit_moves_toward_better_loss(ctx):
+    """A few Adam steps of the training loop on a small problem lower the exact loss."""
+    from paper_2207_06856_gb300 import autograd, gpk
+    X, y, ls, a2, s2, M, kern = _problem(N=1000, d=3, M=8, seed=5)
+    oh0 = O.Hyp("rbf", np.full(3, 2.5), 1.0, 0.3)
+    hist = autograd.fit(ctx, _dev(X), _dev(y), gpk.RBF, np.full(3, 2.5), 1.0, 0.3, steps=15, lr=0.1, M=8,
+                        rank=20, tol=1e-2, max_iter=200, precision="fp16")
+    l, a, s = hist[-1][1], hist[-1][2], hist[-1][3]
+    assert O.mll_exact(X, y, O.Hyp("rbf", l, a, s)) < O.mll_exact(X, y, oh0)
