@@ -358,6 +358,81 @@ def run_kmvm(args):
                       "avg_launch_ms": ms / max(n, 1), "pairs_per_s": pairs / (ms / max(n, 1) / 1e3)}), flush=True)
 
 
+def run_serve(args):
+    """Serving workload: 512 posterior-mean requests (N log-uniform in [1k, 200k],
+    d in {4, 8, 16}, RBF / Matern-3/2, 1024 test points each), FP16 MVM + CG to
+    1e-2 with a rank-20 preconditioner.  First the saturated throughput is
+    measured (a batch of requests submitted at once), then all requests are
+    replayed with Poisson arrivals at 0.7x that rate; p50 / p99 latency
+    (submit -> result on the host) and completed solves/s are reported."""
+    import torch
+    from paper_2207_06856_gb300 import gpk, workloads
+    torch.cuda.set_device(0)
+    reqs = workloads.serving(n_requests=args.serve_requests, rate_per_s=1.0, seed=1)
+    pin = gpk.Server.pinned
+    inputs = [(gpk.Hyper(r.kernel, r.lengthscale, r.outputscale, r.noise), pin(r.X), pin(r.y), pin(r.Xstar))
+              for r in reqs]
+    srv = gpk.Server(0, arena_bytes=int(args.serve_arena_gb * (1 << 30)), max_slots=args.serve_slots, rank=20,
+                     precision="fp16", mean_precision="fp32", tol=TOL, max_iter=1000, restarts=4)
+    small = workloads.serving(n_requests=3, rate_per_s=1.0, seed=2, n_min=1000, n_max=2000)
+    for r in small:   # warm-up
+        srv.submit(gpk.Hyper(r.kernel, r.lengthscale, r.outputscale, r.noise), r.X, r.y, r.Xstar).result()
+    # saturated throughput: a random subset submitted at once
+    cal = np.random.default_rng(3).choice(len(inputs), min(args.serve_calib, len(inputs)), replace=False)
+    t0 = time.perf_counter()
+    futs = [srv.submit(*inputs[i]) for i in cal]
+    for f in futs:
+        f.result()
+    sat = len(cal) / (time.perf_counter() - t0)
+    rate = args.serve_load * sat
+    sampler = ClockSampler(0)
+    launches0 = srv.stats()["launches"]
+    sampler.start()
+    futs = []
+    t_start = time.perf_counter()
+    for r, inp in zip(reqs, inputs):
+        due = t_start + r.arrival_s / rate
+        now = time.perf_counter()
+        if due > now:
+            time.sleep(due - now)
+        futs.append(srv.submit(*inp))
+    res = [f.result() for f in futs]
+    t_end = time.perf_counter()
+    clocks = sampler.stop()
+    st = srv.stats()
+    lat = np.array([s["latency_ms"] for _, s in res])
+    iters = np.array([s["iters"] for _, s in res])
+    status = [s["status"] for _, s in res]
+    rel = np.array([s["rel_resid"] for _, s in res])
+    # spot check against the FP64 oracle on the smallest requests (untimed)
+    import oracle as O
+    check = []
+    for i in np.argsort([r.X.shape[0] for r in reqs])[:3]:
+        r = reqs[i]
+        oh = O.Hyp(workloads.KERNEL_NAMES[r.kernel], r.lengthscale.astype(np.float64), r.outputscale, r.noise)
+        ref = O.kernel_matrix(r.Xstar, r.X, oh) @ O.cholesky_solve(r.X, oh, r.y.astype(np.float64))
+        check.append(float(np.linalg.norm(res[i][0] - ref) / np.linalg.norm(ref)))
+    srv.close()
+    wall = t_end - t_start
+    line = {
+        "metric": "serve_latency_p99", "value": float(np.percentile(lat, 99)), "unit": "ms", "n_gpus": 1,
+        "steps": len(reqs), "warmup": len(small), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "fp16", "data": "synthetic",
+        "config": {"workload": f"serving: {len(reqs)} posterior-mean requests, Poisson arrivals at "
+                               f"{args.serve_load:.2f}x saturated rate, N log-uniform [1k, 200k], d in {{4,8,16}}, "
+                               "RBF/Matern-3/2, 1024 test points, FP16 MVM + stable CG to 1e-2, rank 20",
+                   "slots": args.serve_slots, "arena_gb": args.serve_arena_gb},
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "mean_ms": float(lat.mean()), "solves_per_s": len(reqs) / wall, "saturated_solves_per_s": sat,
+        "offered_rate_per_s": rate, "iters_p50": float(np.median(iters)), "iters_max": int(iters.max()),
+        "all_ok": all(s == gpk.GP_OK for s in status), "rel_resid_max": float(rel.max()),
+        "max_inflight": st["max_inflight"], "arena_peak_gb": st["peak_bytes"] / 2 ** 30,
+        "oracle_mean_relerr_smallest3": check, "gpu_launches": int(st["launches"] - launches0),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -371,10 +446,17 @@ def main():
     ap.add_argument("--skip-verify", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-iters", type=int, default=152)
-    ap.add_argument("--mode", default="solve", choices=["solve", "kmvm"])
+    ap.add_argument("--mode", default="solve", choices=["solve", "kmvm", "serve"])
+    ap.add_argument("--serve-requests", type=int, default=512)
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-arena-gb", type=float, default=48.0)
+    ap.add_argument("--serve-calib", type=int, default=64)
+    ap.add_argument("--serve-load", type=float, default=0.7)
     args = ap.parse_args()
     if args.mode == "kmvm":
         run_kmvm(args)
+    elif args.mode == "serve":
+        run_serve(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -229,6 +229,11 @@ typedef struct {
                             mixed-precision iterative refinement: a half-precision MVM
                             cannot resolve the residual of its own solution when
                             K x cancels heavily (|x| >> |b| for small sigma^2)       */
+    int escalate;        /* nonzero: when a run ends with a breakdown (a non-positive
+                            d^T K d or r^T z: the low-precision operator is not positive
+                            definite to the accuracy the solve has reached), the
+                            true-residual restart continues the solve with the
+                            check_precision MVM.  Needs restarts > 0.                */
 } gp_cg_opts_t;
 
 /* Host-side statistics (every pointer may be NULL). */
@@ -237,6 +242,7 @@ typedef struct {
     int converged;       /* columns that reached tol                          */
     int breakdowns;      /* columns stopped by an LSE breakdown               */
     int restarts;        /* true-residual restarts performed                  */
+    int escalated;       /* 1 if a breakdown moved the solve to check_precision */
     int* col_iters;      /* [R]                                               */
     double* rel_resid;   /* [R] final relative residual: the recomputed one after a
                             true-residual check, else the recursive one           */
@@ -308,6 +314,74 @@ GPK_API int gp_mll_and_grad(gp_ctx* ctx, const gp_hyp_t* hyp, const float* X, co
                             const float* Z, int M, const float* E, const gp_precond_t* precond,
                             const gp_cg_opts_t* opts, int flags, double* mll, double* grad, float* grad_X,
                             float* U, gp_cg_stats_t* stats, void* stream);
+
+/* ---- S8: serving with continuous batching (predictive mean, Sec. 2.1) ------- *
+ * A server owns one device arena (allocated once by gp_server_create, never
+ * grown) and a fixed number of request slots, each with its own CUDA stream.
+ * An engine thread admits queued requests in arrival order whenever a slot is
+ * free and the request's exact footprint (gp_server_request_bytes) fits in the
+ * arena's free space, then advances every admitted request one phase at a time
+ * without blocking: upload -> pivoted-Cholesky preconditioner -> one stable-CG
+ * iteration per phase (Alg. 2, Eq. woodbury) -> true-residual checks ->
+ * predictive mean mu* = K(X*, X) v with v = Ktilde^{-1} y (the posterior mean
+ * of Sec. 2.1, a rectangular kernel MVM) -> download.  Requests arriving while
+ * others run are admitted as slots and memory free up, and the phases of all
+ * admitted requests overlap on the device.  A request's arithmetic does not
+ * depend on what else is in flight: its result is the same alone and in a mix.
+ */
+typedef struct {
+    size_t arena_bytes;  /* device memory for all admitted requests (> 0)         */
+    int max_slots;       /* requests in flight at once, 1..64                      */
+    int rank;            /* pivoted-Cholesky rank per request, 0..512 (0: none)     */
+    int precision;       /* MVM precision inside CG: GP_PREC_* (and GP_MVM_* flags) */
+    int mean_precision;  /* precision of the predictive-mean MVM                    */
+    double tol;          /* CG relative-residual tolerance                          */
+    int max_iter;        /* CG iteration limit (bounds the re-orthogonalisation store) */
+    int restarts;        /* FP32 true-residual checks, 0..16                        */
+    int reorth;          /* GP_REORTH_*                                             */
+} gp_server_opts_t;
+
+typedef struct {
+    int status;          /* GP_OK, GP_ERR_NOT_CONVERGED (mean still written), ...   */
+    int iters;           /* CG iterations                                           */
+    int restarts;        /* true-residual checks taken                              */
+    double rel_resid;    /* final ||Ktilde v - y|| / ||y|| (FP32 check MVM)         */
+    double t_submit_ms;  /* host clock, ms since gp_server_create                   */
+    double t_admit_ms;
+    double t_done_ms;    /* engine saw the download complete                        */
+    size_t bytes;        /* the request's arena footprint                           */
+} gp_request_stats_t;
+
+typedef struct {
+    uint64_t submitted, completed;
+    size_t arena_bytes;   /* budget                                                */
+    size_t peak_bytes;    /* largest arena use seen (never above arena_bytes)      */
+    size_t in_use_bytes;
+    int max_inflight;     /* most requests admitted at once                        */
+    int64_t launches;     /* kernels launched for requests                         */
+} gp_server_stats_t;
+
+typedef struct gp_server gp_server;
+
+/* Exact arena footprint of one request (0 for invalid arguments). */
+GPK_API size_t gp_server_request_bytes(const gp_server_opts_t* opts, const gp_hyp_t* hyp, int64_t N, int64_t n_test);
+/* Allocates the arena and the slots' streams, starts the engine thread. */
+GPK_API int gp_server_create(int device, const gp_server_opts_t* opts, gp_server** out);
+/* Queues one request; returns at once.  Host buffers (X: N x d row-major,
+ * y: N, X_test: n_test x d row-major, mean_out: n_test) are owned by the caller
+ * and must stay valid until gp_server_wait returns for this id; page-locked
+ * buffers make the copies asynchronous.  hyp->lengthscale is copied.
+ * GP_ERR_WORKSPACE if the footprint exceeds the whole arena (never admissible),
+ * GP_ERR_INVALID for bad arguments or a stopped server. */
+GPK_API int gp_server_submit(gp_server* srv, const gp_hyp_t* hyp, const float* X, int64_t N, const float* y,
+                             const float* X_test, int64_t n_test, float* mean_out, uint64_t* id_out);
+/* Blocks until request `id` completes (timeout_s < 0: no limit) and returns
+ * its status (GP_ERR_TIMEOUT when the host wait ran out, the request is then
+ * still pending and may be waited for again).  Each id is reported once. */
+GPK_API int gp_server_wait(gp_server* srv, uint64_t id, double timeout_s, gp_request_stats_t* stats);
+GPK_API int gp_server_stats(gp_server* srv, gp_server_stats_t* out);
+/* Finishes every queued and admitted request, stops the engine, frees all. */
+GPK_API void gp_server_destroy(gp_server* srv);
 
 #ifdef __cplusplus
 }

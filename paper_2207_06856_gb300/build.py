@@ -69,7 +69,7 @@ def build(verbose_ptxas: bool = False, jobs: int | None = None) -> str:
     newest_obj = max(os.path.getmtime(o) for o in objs)
     if not os.path.exists(LIB) or os.path.getmtime(LIB) < newest_obj:
         tmp = LIB + ".tmp"
-        cmd = [_nvcc(), ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fPIC"]
+        cmd = [_nvcc(), ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fPIC", "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -32,6 +32,7 @@
 
 #include <math.h>
 #include <string.h>
+#include <vector>
 
 namespace gpk {
 
@@ -42,17 +43,6 @@ constexpr int kDotPerThread = 8;
 constexpr int kDotChunk = kDotThreads * kDotPerThread;
 constexpr int kEmptyExp = -100000;
 
-struct ColState {
-    double log_gamma;   // log r^T z (both algorithms keep it; Alg. 1 also keeps gamma)
-    double gamma;
-    double alpha, beta;
-    double bnorm, rnorm, relres;
-    double gamma0;      // r_0^T z_0 (the SLQ quadrature weight ||P^{-1/2} r_0||^2)
-    int active;
-    int iters;
-    int breakdown;
-    int pad;
-};
 
 struct Lse {
     double s;
@@ -209,6 +199,7 @@ __global__ void scalar_kernel(int mode, int stable, const double* __restrict__ p
                     }
                 }
                 if (S.active) atomicAdd(&cnt, 1);
+                if (S.breakdown && n_active) atomicAdd(&n_active[1], 1);   // breakdowns of this run
             }
         }
     }
@@ -339,14 +330,6 @@ __global__ void active_flags_kernel(const ColState* __restrict__ st, int R, int*
     if (c < R) flags[c] = st[c].active;
 }
 
-struct CgBufs {
-    float *r, *z, *d, *Kd, *rho, *zeta;
-    double *dpart, *gpart, *coef, *ahist, *bhist, *rhist;
-    ColState* st;
-    int* nact;
-    int* aflags;
-    int nb_max, nblk_dot;
-};
 
 int vec_grid(const Ctx* ctx, int64_t N) {
     int64_t g = (N + 255) / 256;
@@ -377,6 +360,7 @@ void cg_layout(A& a, const Ctx* ctx, int64_t N, int R, int rank, const gp_cg_opt
     a.template take<ColState>((size_t)R);
     a.template take<int>(4);
     a.template take<int>((size_t)R);
+    a.template take<int>((size_t)R);
     (void)ctx;
     (void)rank;
 }
@@ -405,192 +389,260 @@ size_t cg_workspace(const Ctx* ctx, const gp_hyp_t* hyp, int64_t N, int R, int r
     return s;
 }
 
-int cg_run(Ctx* ctx, WsCarver& wc, const gp_hyp_t* hyp, const float* X, int64_t N, const float* B, int R,
-           float* U, const gp_precond_t* pc, const gp_cg_opts_t* o, gp_cg_stats_t* stats, cudaStream_t s) {
-    const int stable = o->algorithm == GP_CG_STABLE;
-    const int reorth = stable ? o->reorth : GP_REORTH_NONE;
-    const int passes = o->reorth_passes >= 2 ? 2 : 1;
+// ---- step-able solver ---------------------------------------------------------------
+// The solve is a sequence of enqueued phases (set-up, one iteration, a
+// true-residual check), each ending with an asynchronous copy of the number of
+// still-active columns into pinned host memory.  step() decides the next phase
+// from that number once the previous phase has completed, so a caller may
+// block on it (gp_cg_solve) or poll an event and interleave many solves.
+
+int CgSolver::launched(int n) {
+    ctx->launches += n;
+    return cudaGetLastError() == cudaSuccess ? GP_OK : GP_ERR_CUDA;
+}
+
+int CgSolver::flag_copy() {
+    // [0] active columns, [1] breakdown count of the current run
+    if (cudaMemcpyAsync(flag_host, b.nact, 2 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return GP_ERR_CUDA;
+    if (ev && cudaEventRecord(ev, s) != cudaSuccess) return GP_ERR_CUDA;
+    return GP_OK;
+}
+
+int CgSolver::wait() {
+    const cudaError_t e = ev ? cudaEventSynchronize(ev) : cudaStreamSynchronize(s);
+    return e == cudaSuccess ? GP_OK : GP_ERR_CUDA;
+}
+
+int CgSolver::precond(const float* W, float* Z, bool masked) {
+    const dim3 gcol((unsigned)vg, (unsigned)R);
+    if (rank == 0) {
+        copy_active_kernel<<<gcol, 256, 0, s>>>(Z, W, N, masked ? b.st : nullptr);
+        return launched(1);
+    }
+    if (masked) {
+        active_flags_kernel<<<1, 64, 0, s>>>(b.st, R, b.aflags);
+        GPK_TRY(launched(1));
+    }
+    WsCarver wtmp = wc_rest;   // Woodbury scratch beyond the solver's buffers
+    return woodbury_apply(ctx, wtmp, pc.L, pc.core, rank, hyp.noise, N, W, R, masked ? b.aflags : nullptr, Z, s);
+}
+
+int CgSolver::dots(const float* A, const float* Bv, bool masked) {
+    dots_kernel<<<dim3((unsigned)b.nblk_dot, (unsigned)R), kDotThreads, 0, s>>>(A, Bv, N, b.nblk_dot,
+                                                                                 masked ? b.aflags : nullptr, b.dpart);
+    return launched(1);
+}
+
+int CgSolver::scalar(int mode, int kk) {
+    scalar_kernel<<<1, 1024, 0, s>>>(mode, stable, b.dpart, b.nblk_dot, R, b.st, kk, o.tol, o.min_iter, b.ahist,
+                                     b.bhist, b.rhist, b.nact);
+    return launched(1);
+}
+
+int CgSolver::start(bool from_x, int k0) {
+    const dim3 gcol((unsigned)vg, (unsigned)R);
     const size_t NR = (size_t)N * R;
-    CgBufs b;
+    GPK_CUDA_TRY(cudaMemsetAsync(b.nact, 0, 2 * sizeof(int), s));
+    if (from_x) {
+        // the first start uses the solve's MVM; a restart the check MVM
+        GPK_TRY(kop_apply(ctx, k0 > 0 ? *op_chk : op, U, R, b.Kd, N, true, s));
+        init_r_kernel<<<vg, 256, 0, s>>>(b.r, b.Kd, B, U, (int64_t)NR, 0);
+    } else {
+        init_r_kernel<<<vg, 256, 0, s>>>(b.r, nullptr, B, U, (int64_t)NR, 1);
+    }
+    GPK_TRY(launched(1));
+    GPK_TRY(precond(b.r, b.z, false));
+    GPK_TRY(dots(b.r, b.z, false));
+    GPK_TRY(scalar(SC_INIT, k0));
+    update_d_kernel<<<gcol, 256, 0, s>>>(b.d, b.z, b.r, N, b.st, 1, reorth, b.rho, b.zeta);
+    GPK_TRY(launched(1));
+    return flag_copy();
+}
+
+int CgSolver::iterate() {
+    const dim3 gcol((unsigned)vg, (unsigned)R);
+    const dim3 gdot((unsigned)b.nblk_dot, (unsigned)R);
+    const size_t NR = (size_t)N * R;
+    // Kd = Ktilde d
+    GPK_TRY(kop_apply(ctx, escalated ? *op_chk : op, b.d, R, b.Kd, N, true, s));
+    active_flags_kernel<<<1, 64, 0, s>>>(b.st, R, b.aflags);
+    GPK_TRY(launched(1));
+    GPK_TRY(dots(b.d, b.Kd, true));
+    GPK_TRY(scalar(SC_ALPHA, k));
+    update_xr_kernel<<<gcol, 256, 0, s>>>(U, b.r, b.d, b.Kd, N, b.st);
+    GPK_TRY(launched(1));
+    if (reorth != GP_REORTH_NONE) {
+        const int nb = k - nb0 + 1;   // basis vectors r_0 .. r_k of this run
+        const float* ZB = reorth == GP_REORTH_PINV ? b.zeta : b.rho;
+        for (int p = 0; p < passes; ++p) {
+            gram_kernel<<<gdot, kDotThreads, 0, s>>>(ZB, nb, R, b.r, N, b.nblk_dot, b.st, b.gpart);
+            gram_finalize_kernel<<<(nb * R + 255) / 256, 256, 0, s>>>(b.gpart, b.nblk_dot, nb, R, b.st, b.coef);
+            reorth_update_kernel<<<gcol, 256, 0, s>>>(b.rho, nb, R, b.coef, b.r, N, b.st);
+            GPK_TRY(launched(3));
+        }
+    }
+    GPK_TRY(precond(b.r, b.z, true));
+    GPK_TRY(dots(b.r, b.z, true));
+    GPK_TRY(scalar(SC_BETA, k));
+    const size_t slot = (size_t)(k - nb0 + 1);
+    float* rho_k = b.rho ? b.rho + slot * NR : nullptr;
+    float* zeta_k = b.zeta ? b.zeta + slot * NR : nullptr;
+    update_d_kernel<<<gcol, 256, 0, s>>>(b.d, b.z, b.r, N, b.st, 0, reorth, rho_k, zeta_k);
+    GPK_TRY(launched(1));
+    ++k;
+    iters = k;
+    return flag_copy();
+}
+
+int CgSolver::setup(Ctx* c, WsCarver& wc, const gp_hyp_t* h, const float* X_, int64_t N_, const float* B_, int R_,
+                    float* U_, const gp_precond_t* pc_, const gp_cg_opts_t* o_, cudaStream_t s_, int* flag_host_,
+                    cudaEvent_t ev_) {
+    ctx = c;
+    s = s_;
+    flag_host = flag_host_;
+    ev = ev_;
+    hyp = *h;
+    X = X_;
+    N = N_;
+    B = B_;
+    R = R_;
+    U = U_;
+    o = *o_;
+    pc = pc_ ? *pc_ : gp_precond_t{nullptr, nullptr, 0};
+    rank = pc.rank > 0 ? pc.rank : 0;
+    stable = o.algorithm == GP_CG_STABLE;
+    reorth = stable ? o.reorth : GP_REORTH_NONE;
+    passes = o.reorth_passes >= 2 ? 2 : 1;
+    const size_t NR = (size_t)N * R;
     b.r = wc.take<float>(NR);
     b.z = wc.take<float>(NR);
     b.d = wc.take<float>(NR);
     b.Kd = wc.take<float>(NR);
-    b.nb_max = o->max_iter + 1;
+    b.nb_max = o.max_iter + 1;
     b.rho = reorth != GP_REORTH_NONE ? wc.take<float>((size_t)b.nb_max * NR) : nullptr;
     b.zeta = reorth == GP_REORTH_PINV ? wc.take<float>((size_t)b.nb_max * NR) : nullptr;
     b.nblk_dot = (int)((N + kDotChunk - 1) / kDotChunk);
     b.dpart = wc.take<double>((size_t)b.nblk_dot * R * 3);
     b.gpart = reorth != GP_REORTH_NONE ? wc.take<double>((size_t)b.nblk_dot * R * b.nb_max) : nullptr;
     b.coef = reorth != GP_REORTH_NONE ? wc.take<double>((size_t)b.nb_max * R) : nullptr;
-    b.ahist = wc.take<double>((size_t)o->max_iter * R);
-    b.bhist = wc.take<double>((size_t)o->max_iter * R);
-    b.rhist = wc.take<double>((size_t)(o->max_iter + 1) * R);
+    b.ahist = wc.take<double>((size_t)o.max_iter * R);
+    b.bhist = wc.take<double>((size_t)o.max_iter * R);
+    b.rhist = wc.take<double>((size_t)(o.max_iter + 1) * R);
     b.st = wc.take<ColState>((size_t)R);
     b.nact = wc.take<int>(4);
     b.aflags = wc.take<int>((size_t)R);
+    b.len0 = wc.take<int>((size_t)R);
     if (!wc.ok) return GP_ERR_WORKSPACE;
-    const int rank = (pc && pc->rank > 0) ? pc->rank : 0;
-
-    KOp op;
-    GPK_TRY(kop_prepare(ctx, wc, op, hyp, X, N, X, N, R, o->precision, s));
-    KOp op_chk_own;
-    KOp* op_chk = &op;
-    if (o->restarts > 0 && o->check_precision != (o->precision & 0xff)) {
-        GPK_TRY(kop_prepare(ctx, wc, op_chk_own, hyp, X, N, X, N, R, o->check_precision, s));
+    GPK_TRY(kop_prepare(ctx, wc, op, &hyp, X, N, X, N, R, o.precision, s));
+    op_chk = &op;
+    if (o.restarts > 0 && o.check_precision != (o.precision & 0xff)) {
+        GPK_TRY(kop_prepare(ctx, wc, op_chk_own, &hyp, X, N, X, N, R, o.check_precision, s));
         op_chk = &op_chk_own;
     }
-
-    const int vg = vec_grid(ctx, N);
-    const dim3 gcol((unsigned)vg, (unsigned)R);
-    const dim3 gdot((unsigned)b.nblk_dot, (unsigned)R);
-    auto launched = [&](int n) { ctx->launches += n; return cudaGetLastError() == cudaSuccess ? GP_OK : GP_ERR_CUDA; };
-    auto precond = [&](const float* W, float* Z, bool masked) -> int {
-        if (rank == 0) {
-            copy_active_kernel<<<gcol, 256, 0, s>>>(Z, W, N, masked ? b.st : nullptr);
-            return launched(1);
-        }
-        if (masked) {
-            active_flags_kernel<<<1, 64, 0, s>>>(b.st, R, b.aflags);
-            GPK_TRY(launched(1));
-        }
-        WsCarver wtmp = wc;   // Woodbury scratch beyond the solver's buffers
-        return woodbury_apply(ctx, wtmp, pc->L, pc->core, rank, hyp->noise, N, W, R, masked ? b.aflags : nullptr, Z, s);
-    };
-    auto dots = [&](const float* A, const float* Bv, bool masked) -> int {
-        dots_kernel<<<gdot, kDotThreads, 0, s>>>(A, Bv, N, b.nblk_dot, masked ? b.aflags : nullptr, b.dpart);
-        return launched(1);
-    };
-    auto scalar = [&](int mode, int k) -> int {
-        scalar_kernel<<<1, 1024, 0, s>>>(mode, stable, b.dpart, b.nblk_dot, R, b.st, k, o->tol, o->min_iter, b.ahist,
-                                         b.bhist, b.rhist, b.nact);
-        return launched(1);
-    };
-
-    // ---- initialisation (and re-initialisation on a true-residual restart) ----
+    wc_rest = wc;
+    vg = vec_grid(ctx, N);
+    k = nb0 = restarts = iters = 0;
+    last_check = false;
+    len_recorded = false;
+    escalated = false;
     GPK_TRY(dots(B, B, false));
     GPK_TRY(scalar(SC_BNORM, 0));
-    auto start = [&](bool from_x, int k0) -> int {
-        if (from_x) {
-            // the first start uses the solve's MVM; a restart the check MVM
-            GPK_TRY(kop_apply(ctx, k0 > 0 ? *op_chk : op, U, R, b.Kd, N, true, s));
-            init_r_kernel<<<vg, 256, 0, s>>>(b.r, b.Kd, B, U, (int64_t)NR, 0);
-        } else {
-            init_r_kernel<<<vg, 256, 0, s>>>(b.r, nullptr, B, U, (int64_t)NR, 1);
-        }
-        GPK_TRY(launched(1));
-        GPK_TRY(precond(b.r, b.z, false));
-        GPK_TRY(dots(b.r, b.z, false));
-        GPK_TRY(scalar(SC_INIT, k0));
-        update_d_kernel<<<gcol, 256, 0, s>>>(b.d, b.z, b.r, N, b.st, 1, reorth, b.rho, b.zeta);
-        GPK_TRY(launched(1));
-        if (cudaMemcpyAsync(ctx->host_pinned, b.nact, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-            return GP_ERR_CUDA;
-        if (cudaStreamSynchronize(s) != cudaSuccess) return GP_ERR_CUDA;
-        return GP_OK;
-    };
-    GPK_TRY(start(o->x0_given != 0, 0));
-    int n_active = ctx->host_pinned[0];
-    int iters = 0, restarts = 0, nb0 = 0;   // nb0: first iteration of the current basis
-    bool first_recorded = false;
+    return start(o.x0_given != 0, 0);
+}
 
-    int k = 0;
-    while (true) {
-        for (; k < o->max_iter && n_active > 0; ++k) {
-            // Kd = Ktilde d
-            GPK_TRY(kop_apply(ctx, op, b.d, R, b.Kd, N, true, s));
-            active_flags_kernel<<<1, 64, 0, s>>>(b.st, R, b.aflags);
-            GPK_TRY(launched(1));
-            GPK_TRY(dots(b.d, b.Kd, true));
-            GPK_TRY(scalar(SC_ALPHA, k));
-            update_xr_kernel<<<gcol, 256, 0, s>>>(U, b.r, b.d, b.Kd, N, b.st);
-            GPK_TRY(launched(1));
-            if (reorth != GP_REORTH_NONE) {
-                const int nb = k - nb0 + 1;   // basis vectors r_0 .. r_k of this run
-                const float* ZB = reorth == GP_REORTH_PINV ? b.zeta : b.rho;
-                for (int p = 0; p < passes; ++p) {
-                    gram_kernel<<<gdot, kDotThreads, 0, s>>>(ZB, nb, R, b.r, N, b.nblk_dot, b.st, b.gpart);
-                    gram_finalize_kernel<<<(nb * R + 255) / 256, 256, 0, s>>>(b.gpart, b.nblk_dot, nb, R, b.st,
-                                                                             b.coef);
-                    reorth_update_kernel<<<gcol, 256, 0, s>>>(b.rho, nb, R, b.coef, b.r, N, b.st);
-                    GPK_TRY(launched(3));
-                }
-            }
-            GPK_TRY(precond(b.r, b.z, true));
-            GPK_TRY(dots(b.r, b.z, true));
-            GPK_TRY(scalar(SC_BETA, k));
-            const size_t slot = (size_t)(k - nb0 + 1);
-            float* rho_k = b.rho ? b.rho + slot * NR : nullptr;
-            float* zeta_k = b.zeta ? b.zeta + slot * NR : nullptr;
-            update_d_kernel<<<gcol, 256, 0, s>>>(b.d, b.z, b.r, N, b.st, 0, reorth, rho_k, zeta_k);
-            GPK_TRY(launched(1));
-            if (cudaMemcpyAsync(ctx->host_pinned, b.nact, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-                return GP_ERR_CUDA;
-            if (cudaStreamSynchronize(s) != cudaSuccess) return GP_ERR_CUDA;
-            n_active = ctx->host_pinned[0];
-            iters = k + 1;
-        }
-        if (restarts == 0 && stats && stats->lanczos_len) {
-            // lengths of the first (unrestarted) run: the Lanczos process its step sizes describe
-            ColState* tmp = (ColState*)malloc(sizeof(ColState) * R);
-            if (!tmp) return GP_ERR_OOM;
-            if (cudaMemcpyAsync(tmp, b.st, sizeof(ColState) * R, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                cudaStreamSynchronize(s) != cudaSuccess) {
-                free(tmp);
-                return GP_ERR_CUDA;
-            }
-            for (int c = 0; c < R; ++c) stats->lanczos_len[c] = tmp[c].iters;
-            free(tmp);
-            first_recorded = true;
-        }
-        if (restarts >= o->restarts || k >= o->max_iter) break;
+// Decide and enqueue the next phase; the previous phase must have completed.
+int CgSolver::step(bool* done) {
+    const int n = *flag_host;
+    *done = false;
+    if (n > 0 && k < o.max_iter) {
+        last_check = false;
+        return iterate();
+    }
+    if (last_check) {   // a true-residual check left nothing to do
+        *done = true;
+        return GP_OK;
+    }
+    if (!len_recorded) {
+        // lengths of the first (unrestarted) run: the Lanczos process its step sizes describe
+        if (cudaMemcpy2DAsync(b.len0, sizeof(int), &b.st[0].iters, sizeof(ColState), sizeof(int), (size_t)R,
+                              cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return GP_ERR_CUDA;
+        len_recorded = true;
+    }
+    if (restarts < o.restarts && k < o.max_iter) {
+        // A breakdown means the MVM's operator is not positive definite to the
+        // accuracy reached: with escalation the rest of the solve uses the
+        // check MVM (the restart below already does).
+        if (o.escalate && flag_host[1] > 0 && op_chk != &op) escalated = true;
         // True-residual check: recompute r = K x - b; columns above tol restart.
         ++restarts;
         nb0 = k;
-        GPK_TRY(start(true, k));
-        n_active = ctx->host_pinned[0];
-        if (n_active == 0) break;
+        last_check = true;
+        return start(true, k);
     }
+    *done = true;
+    return GP_OK;
+}
 
-    // ---- statistics ----
-    ColState* hs = (ColState*)malloc(sizeof(ColState) * R);
-    if (!hs) return GP_ERR_OOM;
-    cudaError_t ce = cudaMemcpyAsync(hs, b.st, sizeof(ColState) * R, cudaMemcpyDeviceToHost, s);
-    if (ce == cudaSuccess && stats) {
-        if (stats->alpha) ce = cudaMemcpyAsync(stats->alpha, b.ahist, sizeof(double) * o->max_iter * R, cudaMemcpyDeviceToHost, s);
-        if (ce == cudaSuccess && stats->beta)
-            ce = cudaMemcpyAsync(stats->beta, b.bhist, sizeof(double) * o->max_iter * R, cudaMemcpyDeviceToHost, s);
-        if (ce == cudaSuccess && stats->resid_hist)
-            ce = cudaMemcpyAsync(stats->resid_hist, b.rhist, sizeof(double) * (o->max_iter + 1) * R,
-                                 cudaMemcpyDeviceToHost, s);
-    }
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
-    if (ce != cudaSuccess) {
-        free(hs);
-        return GP_ERR_CUDA;
-    }
-    int conv = 0, brk = 0, maxit = 0;
+int CgSolver::enqueue_state(ColState* host_st) {
+    return cudaMemcpyAsync(host_st, b.st, sizeof(ColState) * R, cudaMemcpyDeviceToHost, s) == cudaSuccess
+               ? GP_OK : GP_ERR_CUDA;
+}
+
+int CgSolver::summarize(const ColState* hs, gp_cg_stats_t* stats) const {
+    int conv = 0, brk = 0;
     for (int c = 0; c < R; ++c) {
         if (hs[c].breakdown) ++brk;
-        else if (hs[c].relres <= o->tol) ++conv;
-        if (hs[c].iters > maxit) maxit = hs[c].iters;
+        else if (hs[c].relres <= o.tol) ++conv;
     }
     if (stats) {
         stats->iters = iters;
         stats->converged = conv;
         stats->breakdowns = brk;
         stats->restarts = restarts;
+        stats->escalated = escalated ? 1 : 0;
         for (int c = 0; c < R; ++c) {
-            if (stats->lanczos_len && !first_recorded) stats->lanczos_len[c] = hs[c].iters;
             if (stats->col_iters) stats->col_iters[c] = hs[c].iters;
             if (stats->rel_resid) stats->rel_resid[c] = hs[c].relres;
             if (stats->gamma0) stats->gamma0[c] = hs[c].gamma0;
         }
     }
-    free(hs);
-    (void)maxit;
     if (brk > 0) return GP_ERR_BREAKDOWN;
     return conv == R ? GP_OK : GP_ERR_NOT_CONVERGED;
+}
+
+int CgSolver::finish(gp_cg_stats_t* stats) {
+    std::vector<ColState> hs(R);
+    GPK_TRY(enqueue_state(hs.data()));
+    cudaError_t ce = cudaSuccess;
+    if (stats) {
+        if (stats->alpha) ce = cudaMemcpyAsync(stats->alpha, b.ahist, sizeof(double) * o.max_iter * R, cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess && stats->beta)
+            ce = cudaMemcpyAsync(stats->beta, b.bhist, sizeof(double) * o.max_iter * R, cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess && stats->resid_hist)
+            ce = cudaMemcpyAsync(stats->resid_hist, b.rhist, sizeof(double) * (o.max_iter + 1) * R,
+                                 cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess && stats->lanczos_len && len_recorded)
+            ce = cudaMemcpyAsync(stats->lanczos_len, b.len0, sizeof(int) * R, cudaMemcpyDeviceToHost, s);
+    }
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) return GP_ERR_CUDA;
+    if (stats && stats->lanczos_len && !len_recorded)
+        for (int c = 0; c < R; ++c) stats->lanczos_len[c] = hs[c].iters;
+    return summarize(hs.data(), stats);
+}
+
+int cg_run(Ctx* ctx, WsCarver& wc, const gp_hyp_t* hyp, const float* X, int64_t N, const float* B, int R,
+           float* U, const gp_precond_t* pc, const gp_cg_opts_t* o, gp_cg_stats_t* stats, cudaStream_t s) {
+    CgSolver S;
+    GPK_TRY(S.setup(ctx, wc, hyp, X, N, B, R, U, pc, o, s, ctx->host_pinned, nullptr));
+    bool done = false;
+    while (!done) {
+        GPK_TRY(S.wait());
+        GPK_TRY(S.step(&done));
+    }
+    return S.finish(stats);
 }
 
 }  // namespace gpk

@@ -193,6 +193,8 @@ int check_hyp(const gp_hyp_t* hyp);
 
 // ---- preconditioner (precond.cu) ----
 size_t pivchol_workspace(const Ctx* ctx, int64_t N, int d, int rank);
+// rank_out_host null: asynchronous form (no host sync; L zeroed first and the
+// core built at the full width `rank`).
 int pivchol_run(Ctx* ctx, WsCarver& wc, const gp_hyp_t* hyp, const float* X, int64_t N, int rank, float* L,
                 int32_t* piv, double* core, int* rank_out_host, cudaStream_t s);
 size_t woodbury_workspace(const Ctx* ctx, int64_t N, int k, int R);
@@ -202,6 +204,75 @@ int woodbury_apply(Ctx* ctx, WsCarver& wc, const float* L, const double* core, i
 
 // ---- solver (cg.cu), backward (vjp.cu), loss (mll.cu) ----
 size_t cg_workspace(const Ctx* ctx, const gp_hyp_t* hyp, int64_t N, int R, int rank, const gp_cg_opts_t* o);
+
+// Per-column state of the solver (device memory).
+struct ColState {
+    double log_gamma;   // log r^T z (both algorithms keep it; Alg. 1 also keeps gamma)
+    double gamma;
+    double alpha, beta;
+    double bnorm, rnorm, relres;
+    double gamma0;      // r_0^T z_0 (the SLQ quadrature weight ||P^{-1/2} r_0||^2)
+    int active;
+    int iters;
+    int breakdown;
+    int pad;
+};
+
+struct CgBufs {
+    float *r, *z, *d, *Kd, *rho, *zeta;
+    double *dpart, *gpart, *coef, *ahist, *bhist, *rhist;
+    ColState* st;
+    int* nact;
+    int* aflags;
+    int* len0;   // per-column iterations of the first (unrestarted) run
+    int nb_max, nblk_dot;
+};
+
+// Step-able solver.  setup() enqueues the set-up phase; every phase ends with
+// an asynchronous copy of the number of still-active columns to *flag_host
+// and, when ev is given, an event record.  Once that phase has completed
+// (wait() or an event query), step() reads the flag and enqueues the next
+// phase or reports the solve done.  No call blocks except wait() and finish().
+struct CgSolver {
+    Ctx* ctx = nullptr;
+    cudaStream_t s = nullptr;
+    gp_hyp_t hyp{};
+    const float* X = nullptr;
+    const float* B = nullptr;
+    float* U = nullptr;
+    int64_t N = 0;
+    int R = 0;
+    gp_cg_opts_t o{};
+    gp_precond_t pc{};
+    int rank = 0, stable = 0, reorth = 0, passes = 1, vg = 1;
+    CgBufs b{};
+    KOp op, op_chk_own;
+    KOp* op_chk = nullptr;
+    WsCarver wc_rest{nullptr, 0};
+    int* flag_host = nullptr;
+    cudaEvent_t ev = nullptr;
+    int k = 0, nb0 = 0, restarts = 0, iters = 0;
+    bool last_check = false, len_recorded = false, escalated = false;
+
+    int setup(Ctx* c, WsCarver& wc, const gp_hyp_t* h, const float* X, int64_t N, const float* B, int R, float* U,
+              const gp_precond_t* pc, const gp_cg_opts_t* o, cudaStream_t s, int* flag_host, cudaEvent_t ev);
+    int wait();                   // block until the last enqueued phase has completed
+    int step(bool* done);         // enqueue the next phase (or report done)
+    int enqueue_state(ColState* host_st);   // asynchronous D2H of the per-column states
+    // Summary from states copied by enqueue_state; returns the solve's status.
+    int summarize(const ColState* hs, gp_cg_stats_t* stats) const;
+    int finish(gp_cg_stats_t* stats);        // blocking: copy back, summarize
+
+  private:
+    int launched(int n);
+    int flag_copy();
+    int precond(const float* W, float* Z, bool masked);
+    int dots(const float* A, const float* Bv, bool masked);
+    int scalar(int mode, int kk);
+    int start(bool from_x, int k0);
+    int iterate();
+};
+
 int cg_run(Ctx* ctx, WsCarver& wc, const gp_hyp_t* hyp, const float* X, int64_t N, const float* B, int R,
            float* U, const gp_precond_t* pc, const gp_cg_opts_t* o, gp_cg_stats_t* stats, cudaStream_t s);
 size_t vjp_workspace(int64_t N, int d, int R);

@@ -83,11 +83,14 @@ static int kop_plan(const Ctx* ctx, KOp& op, const gp_hyp_t* hyp, int64_t Nr, in
         op.sp = simt_plan(ctx, Nr, Nc, hyp->d, R < 32 ? R : 32);
     } else if (op.prec == GP_PREC_FP16 || op.prec == GP_PREC_BF16) {
         const bool bf = op.prec == GP_PREC_BF16;
-        // Inputs carried as hi + lo by default for BF16 (8-bit significand) and
-        // for FP16 beyond 12 dimensions, where one rounding of |x^| ~ sqrt(d)
-        // moves the distances by a relative 2^-12 sqrt(d).
+        // Inputs carried as hi + lo by default for BF16 (8-bit significand), for
+        // FP16 beyond 12 dimensions, where one rounding of |x^| ~ sqrt(d)
+        // moves the distances by a relative 2^-12 sqrt(d), and for FP16
+        // whenever the split fits in the same contraction width (d <= 4: the
+        // S product costs the same, and close pairs keep their distances).
         int xsplit = (flags & GP_MVM_XSPLIT) ? 1 : 0;
-        if (!(flags & GP_MVM_NO_XSPLIT) && (bf || hyp->d > 12)) xsplit = 1;
+        const bool free_split = make_layout(hyp->d, op.prec, 1, 0, 0).k_pad == make_layout(hyp->d, op.prec, 0, 0, 0).k_pad;
+        if (!(flags & GP_MVM_NO_XSPLIT) && (bf || hyp->d > 12 || free_split)) xsplit = 1;
         if (flags & GP_MVM_NO_XSPLIT) xsplit = 0;
         if (xsplit && make_layout(hyp->d, op.prec, 1, 0, 0).k_pad == 0) xsplit = 0;   // does not fit
         const int single = (flags & GP_MVM_BF16_SINGLE) ? 1 : 0;

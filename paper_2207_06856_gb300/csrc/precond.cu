@@ -349,6 +349,11 @@ int pivchol_run(Ctx* ctx, WsCarver& wc, const gp_hyp_t* hyp, const float* X, int
     fill_kernel<<<G, 256, 0, s>>>(diag, N, a2);
     ctx->launches++;
     if (cudaMemsetAsync(rk, 0xFF, sizeof(int), s) != cudaSuccess) return GP_ERR_CUDA;   // -1 = running
+    // Without a host readback of the reached rank the factor is used at its
+    // full width: columns an early stop leaves unwritten must be zero (they add
+    // nothing to L L^T and an identity block to the core).
+    if (!rank_out_host && cudaMemsetAsync(L, 0, sizeof(float) * (size_t)N * rank, s) != cudaSuccess)
+        return GP_ERR_CUDA;
     const float tol_abs = 1e-6f * a2;
     for (int m = 0; m < rank; ++m) {
         const Cand* cin = (m & 1) ? ca : cb;
@@ -374,12 +379,15 @@ int pivchol_run(Ctx* ctx, WsCarver& wc, const gp_hyp_t* hyp, const float* X, int
         ctx->launches++;
     }
     if (cudaGetLastError() != cudaSuccess) return GP_ERR_CUDA;
-    int rk_host = -1;
-    if (cudaMemcpyAsync(ctx->host_pinned, rk, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return GP_ERR_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return GP_ERR_CUDA;
-    rk_host = ctx->host_pinned[0];
-    const int kr = rk_host < 0 ? rank : rk_host;
-    *rank_out_host = kr;
+    int kr = rank;
+    if (rank_out_host) {
+        if (cudaMemcpyAsync(ctx->host_pinned, rk, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return GP_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return GP_ERR_CUDA;
+        const int rk_host = ctx->host_pinned[0];
+        kr = rk_host < 0 ? rank : rk_host;
+        *rank_out_host = kr;
+    }
     if (kr == 0) return GP_OK;
     const int tiles = (kr + 15) / 16;
     gram_ll_kernel<<<dim3(tiles * tiles, nsplit), 256, 0, s>>>(L, N, kr, nsplit, part);

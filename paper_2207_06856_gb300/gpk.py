@@ -65,12 +65,12 @@ class _CgOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("min_iter", ctypes.c_int),
                 ("precision", ctypes.c_int), ("algorithm", ctypes.c_int), ("reorth", ctypes.c_int),
                 ("reorth_passes", ctypes.c_int), ("x0_given", ctypes.c_int), ("restarts", ctypes.c_int),
-                ("check_precision", ctypes.c_int)]
+                ("check_precision", ctypes.c_int), ("escalate", ctypes.c_int)]
 
 
 class _CgStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("breakdowns", ctypes.c_int),
-                ("restarts", ctypes.c_int),
+                ("restarts", ctypes.c_int), ("escalated", ctypes.c_int),
                 ("col_iters", ctypes.POINTER(ctypes.c_int)), ("rel_resid", ctypes.POINTER(ctypes.c_double)),
                 ("alpha", ctypes.POINTER(ctypes.c_double)), ("beta", ctypes.POINTER(ctypes.c_double)),
                 ("gamma0", ctypes.POINTER(ctypes.c_double)), ("resid_hist", ctypes.POINTER(ctypes.c_double)),
@@ -81,6 +81,24 @@ class _Hyp(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("d", ctypes.c_int),
                 ("lengthscale", ctypes.POINTER(ctypes.c_float)),
                 ("outputscale", ctypes.c_double), ("noise", ctypes.c_double)]
+
+
+class _ServerOpts(ctypes.Structure):
+    _fields_ = [("arena_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int), ("rank", ctypes.c_int),
+                ("precision", ctypes.c_int), ("mean_precision", ctypes.c_int), ("tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("restarts", ctypes.c_int), ("reorth", ctypes.c_int)]
+
+
+class _ReqStats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("rel_resid", ctypes.c_double), ("t_submit_ms", ctypes.c_double), ("t_admit_ms", ctypes.c_double),
+                ("t_done_ms", ctypes.c_double), ("bytes", ctypes.c_size_t)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("arena_bytes", ctypes.c_size_t),
+                ("peak_bytes", ctypes.c_size_t), ("in_use_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int),
+                ("launches", ctypes.c_int64)]
 
 
 _lib = None
@@ -124,6 +142,13 @@ def _declare(lib):
         "gp_cg_solve": (_c_int, [_c_void_p, ctypes.POINTER(_Hyp), _c_void_p, _c_i64, _c_void_p, _c_int, _c_void_p,
                                  ctypes.POINTER(_Precond), ctypes.POINTER(_CgOpts), ctypes.POINTER(_CgStats),
                                  _c_void_p]),
+        "gp_server_request_bytes": (_c_size, [ctypes.POINTER(_ServerOpts), ctypes.POINTER(_Hyp), _c_i64, _c_i64]),
+        "gp_server_create": (_c_int, [_c_int, ctypes.POINTER(_ServerOpts), ctypes.POINTER(_c_void_p)]),
+        "gp_server_submit": (_c_int, [_c_void_p, ctypes.POINTER(_Hyp), _c_void_p, _c_i64, _c_void_p, _c_void_p,
+                                      _c_i64, _c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
+        "gp_server_wait": (_c_int, [_c_void_p, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(_ReqStats)]),
+        "gp_server_stats": (_c_int, [_c_void_p, ctypes.POINTER(_ServerStats)]),
+        "gp_server_destroy": (None, [_c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -321,7 +346,7 @@ def pivchol(ctx: Context, hyp: Hyper, X, rank: int, stream=None) -> Precond:
 def cg_solve(ctx: Context, hyp: Hyper, X, B, precond: Precond | None = None, tol: float = 1e-2,
              max_iter: int = 50, min_iter: int = 0, precision="fp16", algorithm: str = "stable",
              reorth: str = "pinv", reorth_passes: int = 1, U=None, flags: int = 0, restarts: int = 4,
-             check_precision="fp32", stream=None):
+             check_precision="fp32", escalate: bool = True, stream=None):
     """gp_cg_solve: (K + sigma^2 I) U = B.  B (R, N) -> (U (R, N), status, info).
     info holds the per-column iterations, relative residuals, alpha/beta
     histories (numpy arrays) and gamma_0.  status is GP_OK,
@@ -334,7 +359,8 @@ def cg_solve(ctx: Context, hyp: Hyper, X, B, precond: Precond | None = None, tol
                    CG_STABLE if algorithm == "stable" else CG_STANDARD,
                    REORTH[reorth] if isinstance(reorth, str) else int(reorth), int(reorth_passes),
                    1 if U is not None else 0, int(restarts),
-                   PRECISIONS[check_precision] if isinstance(check_precision, str) else int(check_precision))
+                   PRECISIONS[check_precision] if isinstance(check_precision, str) else int(check_precision),
+                   1 if escalate else 0)
     h = hyp.c()
     rank = precond.rank if precond is not None else 0
     need = int(lib().gp_cg_workspace_size(ctypes.byref(h), N, R, rank, ctypes.byref(opts)))
@@ -352,7 +378,7 @@ def cg_solve(ctx: Context, hyp: Hyper, X, B, precond: Precond | None = None, tol
     rh = np.zeros((max_iter + 1) * R, np.float64)
     P = ctypes.POINTER
     lz = np.zeros(R, np.int32)
-    stats = _CgStats(0, 0, 0, 0, col_iters.ctypes.data_as(P(ctypes.c_int)), rel.ctypes.data_as(P(ctypes.c_double)),
+    stats = _CgStats(0, 0, 0, 0, 0, col_iters.ctypes.data_as(P(ctypes.c_int)), rel.ctypes.data_as(P(ctypes.c_double)),
                      al.ctypes.data_as(P(ctypes.c_double)), be.ctypes.data_as(P(ctypes.c_double)),
                      g0.ctypes.data_as(P(ctypes.c_double)), rh.ctypes.data_as(P(ctypes.c_double)),
                      lz.ctypes.data_as(P(ctypes.c_int)))
@@ -364,7 +390,7 @@ def cg_solve(ctx: Context, hyp: Hyper, X, B, precond: Precond | None = None, tol
         _check(st, "gp_cg_solve")
     it = int(stats.iters)
     info = {"iters": it, "converged": int(stats.converged), "breakdowns": int(stats.breakdowns),
-            "restarts": int(stats.restarts),
+            "restarts": int(stats.restarts), "escalated": int(stats.escalated),
             "col_iters": col_iters, "rel_resid": rel, "gamma0": g0,
             "alpha": al.reshape(max_iter, R)[:it], "beta": be.reshape(max_iter, R)[:it],
             "resid_hist": rh.reshape(max_iter + 1, R)[:it + 1], "lanczos_len": lz}
@@ -434,7 +460,7 @@ def slq_quadrature(alpha, beta, gamma0: float) -> float:
 def mll_and_grad(ctx: Context, hyp: Hyper, X, y, Z, precond: Precond | None = None, E=None,
                  precond_probes: bool = False, want_logdet: bool = True, tol: float = 1e-2, max_iter: int = 100,
                  precision="fp16", want_X: bool = False, return_U: bool = False, restarts: int = 4,
-                 check_precision="fp32", stream=None):
+                 check_precision="fp32", escalate: bool = True, stream=None):
     """gp_mll_and_grad.  X (N, d), y (N,), Z (M, N) probes [, E (M, rank) normals]
     -> (mll, grad (numpy, d + 2), grad_X or None, U or None, info)."""
     import torch
@@ -443,7 +469,8 @@ def mll_and_grad(ctx: Context, hyp: Hyper, X, y, Z, precond: Precond | None = No
     R = M + 1
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     opts = _CgOpts(float(tol), int(max_iter), 0, prec, CG_STABLE, REORTH_PINV, 1, 0, int(restarts),
-                   PRECISIONS[check_precision] if isinstance(check_precision, str) else int(check_precision))
+                   PRECISIONS[check_precision] if isinstance(check_precision, str) else int(check_precision),
+                   1 if escalate else 0)
     h = hyp.c()
     rank = precond.rank if precond is not None else 0
     need = int(lib().gp_mll_workspace_size(ctypes.byref(h), N, M, rank, ctypes.byref(opts)))
@@ -461,7 +488,7 @@ def mll_and_grad(ctx: Context, hyp: Hyper, X, y, Z, precond: Precond | None = No
     g0 = np.zeros(R, np.float64)
     lz = np.zeros(R, np.int32)
     Pd, Pi = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
-    stats = _CgStats(0, 0, 0, 0, col_iters.ctypes.data_as(Pi), rel.ctypes.data_as(Pd), None, None,
+    stats = _CgStats(0, 0, 0, 0, 0, col_iters.ctypes.data_as(Pi), rel.ctypes.data_as(Pd), None, None,
                      g0.ctypes.data_as(Pd), None, lz.ctypes.data_as(Pi))
     pc = precond.c() if precond is not None else _Precond(None, None, 0)
     st = lib().gp_mll_and_grad(ctx.ptr, ctypes.byref(h), _dev_ptr(X, "X", (N, d)), _dev_ptr(y, "y", (N,)), N,
@@ -474,3 +501,101 @@ def mll_and_grad(ctx: Context, hyp: Hyper, X, y, Z, precond: Precond | None = No
     info = {"iters": int(stats.iters), "converged": int(stats.converged), "restarts": int(stats.restarts),
             "col_iters": col_iters, "rel_resid": rel, "gamma0": g0, "lanczos_len": lz}
     return float(mll.value), g, gX, U, info
+
+
+# ---- S8: serving ------------------------------------------------------------------
+
+
+def _server_opts(arena_bytes, max_slots, rank, precision, mean_precision, tol, max_iter, restarts, reorth):
+    return _ServerOpts(int(arena_bytes), int(max_slots), int(rank), PRECISIONS.get(precision, precision),
+                       PRECISIONS.get(mean_precision, mean_precision), float(tol), int(max_iter), int(restarts),
+                       REORTH.get(reorth, reorth))
+
+
+class ServeFuture:
+    """Handle of one submitted request; result() blocks until it completes."""
+
+    def __init__(self, server, rid, keep, mean):
+        self._server, self.id, self._keep, self._mean = server, rid, keep, mean
+        self._done = None
+
+    def result(self, timeout: float | None = None):
+        """(mean (n_test,) float32 numpy array, stats dict); raises GPKError for a
+        failed request (GP_ERR_NOT_CONVERGED is reported in stats, not raised)."""
+        if self._done is None:
+            st = _ReqStats()
+            rc = lib().gp_server_wait(self._server._h, ctypes.c_uint64(self.id),
+                                      -1.0 if timeout is None else float(timeout), ctypes.byref(st))
+            if rc == GP_ERR_TIMEOUT and st.t_done_ms == 0.0 and timeout is not None:
+                raise TimeoutError(f"request {self.id} still running after {timeout} s")
+            stats = {"status": st.status, "iters": st.iters, "restarts": st.restarts, "rel_resid": st.rel_resid,
+                     "t_submit_ms": st.t_submit_ms, "t_admit_ms": st.t_admit_ms, "t_done_ms": st.t_done_ms,
+                     "latency_ms": st.t_done_ms - st.t_submit_ms, "bytes": int(st.bytes)}
+            self._done = (self._mean.numpy().copy(), stats)
+            self._keep = None
+            if st.status not in (GP_OK, GP_ERR_NOT_CONVERGED):
+                raise GPKError(st.status, f"request {self.id}")
+        return self._done
+
+
+class Server:
+    """Continuous-batching GP posterior-mean server (gp_server_*).
+
+    Each request solves (K + sigma^2 I) v = y with the stable preconditioned CG
+    and returns mu* = K(X*, X) v.  Inputs are copied into page-locked host
+    tensors at submit so the library's uploads are asynchronous."""
+
+    def __init__(self, device: int = 0, arena_bytes: int = 8 << 30, max_slots: int = 8, rank: int = 20,
+                 precision="fp16", mean_precision="fp32", tol: float = 1e-2, max_iter: int = 1000,
+                 restarts: int = 4, reorth="pinv"):
+        self.opts = _server_opts(arena_bytes, max_slots, rank, precision, mean_precision, tol, max_iter, restarts,
+                                 reorth)
+        h = _c_void_p()
+        _check(lib().gp_server_create(int(device), ctypes.byref(self.opts), ctypes.byref(h)), "gp_server_create")
+        self._h = h
+
+    def request_bytes(self, hyp: Hyper, N: int, n_test: int) -> int:
+        hc = hyp.c()
+        return int(lib().gp_server_request_bytes(ctypes.byref(self.opts), ctypes.byref(hc), int(N), int(n_test)))
+
+    @staticmethod
+    def pinned(a):
+        """A page-locked contiguous float32 host tensor holding `a` (returned
+        as is when it already is one)."""
+        import torch
+        if isinstance(a, torch.Tensor) and not a.is_cuda and a.dtype == torch.float32 and a.is_contiguous() \
+                and a.is_pinned():
+            return a
+        return torch.as_tensor(np.ascontiguousarray(np.asarray(a), dtype=np.float32)).pin_memory()
+
+    def submit(self, hyp: Hyper, X, y, X_test) -> ServeFuture:
+        """Queue one request (X (N, d), y (N,), X_test (n_test, d)); returns a
+        ServeFuture.  Page-locked float32 tensors are used in place."""
+        import torch
+        X, y, Xs = self.pinned(X), self.pinned(y), self.pinned(X_test)
+        N, d = X.shape
+        n_test = Xs.shape[0]
+        if y.shape != (N,) or Xs.shape[1] != d or hyp.d != d:
+            raise ValueError("shape mismatch between X, y, X_test and the lengthscales")
+        mean = torch.empty(n_test, dtype=torch.float32).pin_memory()
+        hc = hyp.c()
+        rid = ctypes.c_uint64()
+        _check(lib().gp_server_submit(self._h, ctypes.byref(hc), X.data_ptr(), int(N), y.data_ptr(), Xs.data_ptr(),
+                                      int(n_test), mean.data_ptr(), ctypes.byref(rid)), "gp_server_submit")
+        return ServeFuture(self, rid.value, (X, y, Xs, hc), mean)
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check(lib().gp_server_stats(self._h, ctypes.byref(st)), "gp_server_stats")
+        return {k: getattr(st, k) for k, _ in _ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().gp_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
