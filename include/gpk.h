@@ -78,10 +78,16 @@ extern "C" {
                                        (Sec. 4.1) instead of the per-column power
                                        of two                                     */
 #define GP_MVM_VSPLIT       0x1000  /* FP16: carry v as hi + lo (robust to heavy
-                                       cancellation in K v; BF16 always does)     */
+                                       cancellation in K v; BF16 always does, and
+                                       so does FP16 on the pair engine, where it
+                                       costs no extra tensor-core instruction)   */
 #define GP_MVM_BF16_SINGLE  0x2000  /* BF16: single-term kernel tile and v (faster,
                                        ~2^-8 rounding; the default carries both as
                                        hi + lo so the MVM meets 2e-3)             */
+#define GP_MVM_ONE_TILE     0x4000  /* tensor-core MVM on the one-row-tile engine
+                                       (P V with M = 128 rows, N = R) instead of
+                                       the default pair engine (transposed
+                                       V^T P^T, N = 256 rows); for comparison     */
 
 /* GP hyperparameters theta = (l_1..l_d, a^2, sigma^2)   (Sec. 2.2, Eq. mvm) */
 typedef struct {

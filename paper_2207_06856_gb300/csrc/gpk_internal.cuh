@@ -133,12 +133,23 @@ struct MvmArgs {
 struct TcPlan {
     int n_it = 0, n_jt = 0, n_split = 1, grid = 0, R_pad = 0, k_pad = 0;
     int64_t Nr_pad = 0, Nc_pad = 0;
+    int engine = 0;   // 0: one row tile per item (kmvm_tc.cu); 1: row-tile pairs, transposed P.V (kmvm_tp.cu)
+    int rv = 0;       // engine 1: rows of Vt per tile (R_pad, or 2 R_pad with the hi + lo split)
 };
 TcPlan tc_plan(const Ctx* ctx, int64_t Nr, int64_t Nc, int R, int k_pad);
 int tc_smem_bytes(int k_pad, int R_pad, int vsplit);
 int tc_stages(int k_pad, int R_pad, int vsplit);
 size_t tc_partial_floats(const TcPlan& p);
 int launch_kmvm_tc(Ctx* ctx, const TcPlan& plan, const OperandLayout& L, const MvmArgs& a, const CUtensorMap& tmA,
+                   const CUtensorMap& tmB, const CUtensorMap& tmV, const float* outscale, float* partial,
+                   cudaStream_t s);
+
+// Tensor-core engine with the transposed value product (kmvm_tp.cu).  n_it
+// counts pairs of 128-row tiles; the partial buffer is always used.
+bool tp_supported(int k_pad, int R_pad, int vsplit);
+TcPlan tp_plan(const Ctx* ctx, int64_t Nr, int64_t Nc, int R, int k_pad, int vsplit);
+size_t tp_partial_floats(const TcPlan& p);
+int launch_kmvm_tp(Ctx* ctx, const TcPlan& plan, const OperandLayout& L, const MvmArgs& a, const CUtensorMap& tmA,
                    const CUtensorMap& tmB, const CUtensorMap& tmV, const float* outscale, float* partial,
                    cudaStream_t s);
 

@@ -1,0 +1,527 @@
+// S2: the tensor-core kernel MVM with the transposed value product
+// (Eq. mvm; Sec. 4.1).
+//
+//   out_i = a^2 sum_j k(x_i, x_j) v_j (+ sigma^2 v_i)
+//
+// Same dataflow as kmvm_tc.cu (S = XA_i XB_j^T on the tensor cores with the
+// norm terms folded into the contraction, the kernel function on the special
+// function units, an FP32 accumulation of P V in TMEM), but the value product
+// is computed transposed, for two row tiles at once:
+//
+//   O^T (rows r, columns i) += Vt_j (r x 128) . P_j^T      M = 128, N = 256, K = 128
+//
+// A tcgen05.mma occupies the issue path for about the same time whatever its
+// N, so the plain orientation (M = 128 rows i, N = R_pad <= 64) spends eight
+// narrow instructions per 128 x 128 tile on P V.  Transposed, one instruction
+// covers 256 rows i, and the right-hand sides' hi and lo parts (rows
+// [0, R_pad) and [R_pad, 2 R_pad) of Vt) share M, so carrying V as hi + lo
+// costs no extra instruction.  P is the B operand and therefore lives in
+// shared memory: each epilogue thread writes its row of P as 16-byte chunks in
+// the 128-byte-swizzled K-major layout the MMA reads (chunk c of row n at
+// physical chunk c ^ (n mod 8)), then fences to the async proxy.
+//
+// Work item = (pair of 128-row tiles, column split).  Warps: 0-3 epilogue of
+// row tile 0, 4-7 epilogue of row tile 1, 8 TMA producer, 9 MMA issuer and
+// TMEM owner.  TMEM: S of tile 0 [0,128), S of tile 1 [128,256), O^T
+// [256,512).  Shared memory: the X_j / Vt_j stage ring first, then two P
+// buffers of 64 KB, then the row-tile buffers.  The A operand of the value
+// product spans 128 rows of which the first rv = R_pad (1 + vsplit) hold Vt;
+// the rest reads the following shared memory (the next K-block, stage or P
+// buffer: always inside the allocation) and lands in accumulator rows that
+// are never read.
+//
+// O^T rows are written raw to the partial buffer [n_split][rv][ld_part]; the
+// split reduction sums the column splits and the hi / lo rows, scales by
+// a^2 / s_c and adds sigma^2 v.  Every mbarrier wait is bounded; a wait that
+// runs out records DEV_TIMEOUT, drains what was issued, frees TMEM and exits.
+#include "gpk_internal.cuh"
+#include "ptx.cuh"
+#include "kfun.cuh"
+
+namespace gpk {
+
+namespace {
+
+constexpr int kBM = 128;
+constexpr int kBN = 128;
+constexpr int kPairRows = 256;
+constexpr int kMaxStages = 6;
+constexpr int kThreads = 320;
+constexpr int kTmaWarp = 8;
+constexpr int kMmaWarp = 9;
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kTmemO = 256;
+constexpr uint32_t kPKBlock = (uint32_t)kPairRows * 128u;   // one 64-column K-block of P: 256 rows x 128 B
+constexpr uint32_t kPBytes = 2u * kPKBlock;                  // one P buffer (128 columns)
+constexpr int kMaxSmemBytes = 227 * 1024;   // opt-in maximum per CTA (512 B kept for static shared memory)
+
+struct TpParams {
+    int n_ip, n_jt, n_split, n_items;
+    int k_pad, rv;        // rv: rows of Vt per tile (R_pad, or 2 R_pad with the hi + lo split)
+    int stages, xi_bufs;
+    int diag;             // square Matern-1/2 operator: P_ii = 0 on chip (exact diagonal added later)
+    int64_t ld_part;      // n_ip * 256
+    float* partial;       // [n_split][rv][ld_part]
+    int* err;
+    uint64_t limit_ns;
+};
+
+struct TpBarriers {
+    uint64_t full[kMaxStages];
+    uint64_t empty[kMaxStages];
+    uint64_t s_full[2];     // per row tile (epilogue warpgroup)
+    uint64_t s_empty[2];
+    uint64_t p_full[2];     // per P buffer
+    uint64_t p_empty[2];
+    uint64_t o_full;
+    uint64_t o_empty;
+    uint64_t xi_full[2];
+    uint64_t xi_empty[2];
+    uint64_t drain;
+};
+
+__device__ __forceinline__ void record_error(int* err, int code) { atomicCAS(err, 0, code); }
+
+__device__ __forceinline__ void item_range(const TpParams& p, int item, int& ip, int& sp, int& j0, int& j1) {
+    ip = item % p.n_ip;
+    sp = item / p.n_ip;
+    j0 = (int)(((int64_t)sp * p.n_jt) / p.n_split);
+    j1 = (int)(((int64_t)(sp + 1) * p.n_jt) / p.n_split);
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
+                 : "memory");
+}
+
+// ---- TMA producer (one thread) ------------------------------------------------
+__device__ void tp_producer(const TpParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB,
+                            const CUtensorMap* tmV, TpBarriers& bars, uint8_t* sSt, uint8_t* sXi, uint32_t xbytes,
+                            uint32_t vtbytes) {
+    uint32_t fills = 0, xi_loads = 0;
+    bool ok = true;
+    int ic = 0;
+    const uint32_t S = (uint32_t)p.stages;
+    const uint32_t kblk = (uint32_t)p.rv * 128u;
+    for (int item = blockIdx.x; item < p.n_items; item += gridDim.x, ++ic) {
+        int ip, sp, j0, j1;
+        item_range(p, item, ip, sp, j0, j1);
+        const int xb = p.xi_bufs == 2 ? (ic & 1) : 0;
+        const int use = p.xi_bufs == 2 ? (ic >> 1) : ic;   // earlier uses of this buffer
+        if (use >= 1 && !ptx::mbar_wait(&bars.xi_empty[xb], (use - 1) & 1, p.limit_ns)) { ok = false; break; }
+        uint8_t* sX = sXi + (uint32_t)xb * 2u * xbytes;
+        ptx::mbar_arrive_expect_tx(&bars.xi_full[xb], 2u * xbytes);
+        ptx::tma_load_2d(sX, tmA, &bars.xi_full[xb], 0, ip * kPairRows);
+        ptx::tma_load_2d(sX + xbytes, tmA, &bars.xi_full[xb], 0, ip * kPairRows + kBM);
+        ++xi_loads;
+        for (int jt = j0; jt < j1; ++jt) {
+            const uint32_t st = fills % S, u = fills / S;
+            if (u > 0 && !ptx::mbar_wait(&bars.empty[st], (u - 1) & 1, p.limit_ns)) { ok = false; break; }
+            uint8_t* sx = sSt + st * (xbytes + vtbytes);
+            ptx::mbar_arrive_expect_tx(&bars.full[st], xbytes + vtbytes);
+            ptx::tma_load_2d(sx, tmB, &bars.full[st], 0, jt * kBN);
+            ptx::tma_load_2d(sx + xbytes, tmV, &bars.full[st], jt * kBN, 0);
+            ptx::tma_load_2d(sx + xbytes + kblk, tmV, &bars.full[st], jt * kBN + 64, 0);
+            ++fills;
+        }
+        if (!ok) break;
+    }
+    if (!ok) {
+        record_error(p.err, DEV_TIMEOUT);
+        // Let every copy this thread issued land before the CTA can exit.
+        const uint32_t first = fills > S ? fills - S : 0;
+        for (uint32_t f = first; f < fills; ++f) ptx::mbar_wait(&bars.full[f % S], (f / S) & 1, p.limit_ns);
+        const uint32_t nb = (uint32_t)p.xi_bufs;
+        for (uint32_t q = xi_loads > nb ? xi_loads - nb : 0; q < xi_loads; ++q)
+            ptx::mbar_wait(&bars.xi_full[q % nb], (q / nb) & 1, p.limit_ns);
+    }
+}
+
+// ---- MMA issuer (one thread) ----------------------------------------------------
+// Event driven: S(t) for both row tiles once their S buffers have been read
+// and the stage has landed; the value product of tile t once both halves of
+// P(t) are in shared memory (and, first in an item, O has been read out).
+__device__ void tp_mma(const TpParams& p, TpBarriers& bars, const uint8_t* sSt, const uint8_t* sP,
+                       const uint8_t* sXi, uint32_t xbytes, uint32_t vtbytes, uint32_t tmem, uint32_t id_s,
+                       uint32_t id_pv) {
+    const uint32_t arow = (uint32_t)p.k_pad * 2u;                            // 32, 64 or 128 bytes
+    const uint32_t swz = (arow == 32) ? 6u : (arow == 64 ? 4u : 2u);
+    const int ksteps = p.k_pad / 16;
+    const uint32_t S = (uint32_t)p.stages;
+    const uint32_t aSt = ptx::smem_u32(sSt);
+    const uint32_t aP = ptx::smem_u32(sP);
+    const uint32_t stage_bytes = xbytes + vtbytes;
+    const uint32_t kblk = (uint32_t)p.rv * 128u;
+    const long long limit = (long long)(p.limit_ns * 2ull);
+    const uint32_t hi_x = ptx::smem_desc_hi(8u * arow, swz);
+    const uint32_t hi_128 = ptx::smem_desc_hi(1024u, 2u);
+    uint32_t n = 0, gt = 0;
+    int ic = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x, ++ic) {
+        int ip, sp, j0, j1;
+        item_range(p, item, ip, sp, j0, j1);
+        const uint32_t T = (uint32_t)(j1 - j0);
+        const int xb = p.xi_bufs == 2 ? (ic & 1) : 0;
+        const int use = p.xi_bufs == 2 ? (ic >> 1) : ic;
+        if (!ptx::mbar_wait(&bars.xi_full[xb], use & 1, p.limit_ns)) { ok = false; break; }
+        ptx::tc_fence_after();
+        const uint32_t aXi = ptx::smem_u32(sXi) + (uint32_t)xb * 2u * xbytes;
+        uint32_t ts = 0, tp = 0;
+        long long idle_since = clock64();
+        while (tp < T) {
+            bool progressed = false;
+            if (ts < T) {
+                const uint32_t g = gt + ts, f = n + ts, st = f % S;
+                const bool bufs_free = (g == 0) || (ptx::mbar_test(&bars.s_empty[0], (g - 1) & 1) &&
+                                                    ptx::mbar_test(&bars.s_empty[1], (g - 1) & 1));
+                if (bufs_free && ptx::mbar_test(&bars.full[st], (f / S) & 1)) {
+                    ptx::tc_fence_after();
+                    const uint32_t aXj = aSt + st * stage_bytes;
+                    for (int w = 0; w < 2; ++w) {
+                        for (int kk = 0; kk < ksteps; ++kk) {
+                            const uint32_t koff = (uint32_t)kk * 32u;
+                            ptx::mma_f16_ss(tmem + (uint32_t)w * 128u,
+                                            ptx::smem_desc_at(hi_x, aXi + (uint32_t)w * xbytes + koff),
+                                            ptx::smem_desc_at(hi_x, aXj + koff), id_s, kk > 0 ? 1u : 0u);
+                        }
+                        ptx::mma_commit(&bars.s_full[w]);
+                    }
+                    if (ts + 1 == T) ptx::mma_commit(&bars.xi_empty[xb]);   // last use of the row tiles
+                    ++ts;
+                    progressed = true;
+                }
+            }
+            if (tp < ts) {
+                const uint32_t g = gt + tp, pb = g & 1;
+                const bool o_free = (tp > 0) || (ic == 0) || ptx::mbar_test(&bars.o_empty, (ic - 1) & 1);
+                if (o_free && ptx::mbar_test(&bars.p_full[pb], (g >> 1) & 1)) {
+                    ptx::tc_fence_after();
+                    const uint32_t st = (n + tp) % S;
+                    const uint32_t aV = aSt + st * stage_bytes + xbytes;
+                    const uint32_t aPb = aP + pb * kPBytes;
+#pragma unroll
+                    for (int kk = 0; kk < kBN / 16; ++kk) {
+                        const uint32_t kb = (uint32_t)(kk >> 2), ko = (uint32_t)(kk & 3) * 32u;
+                        ptx::mma_f16_ss(tmem + kTmemO, ptx::smem_desc_at(hi_128, aV + kb * kblk + ko),
+                                        ptx::smem_desc_at(hi_128, aPb + kb * kPKBlock + ko), id_pv,
+                                        (tp > 0 || kk > 0) ? 1u : 0u);
+                    }
+                    ptx::mma_commit(&bars.empty[st]);    // X_j and Vt_j of this stage are consumed
+                    ptx::mma_commit(&bars.p_empty[pb]);  // P buffer pb may be rewritten
+                    ++tp;
+                    progressed = true;
+                }
+            }
+            if (progressed) {
+                idle_since = clock64();
+            } else {
+                __nanosleep(64);
+                if (clock64() - idle_since > limit) {
+                    ok = false;
+                    break;
+                }
+            }
+        }
+        if (!ok) break;
+        ptx::mma_commit(&bars.o_full);
+        n += T;
+        gt += T;
+    }
+    ptx::mma_commit(&bars.drain);
+    ptx::mbar_wait(&bars.drain, 0, p.limit_ns);
+    if (!ok) record_error(p.err, DEV_TIMEOUT);
+}
+
+template <int BF16>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+    if constexpr (BF16) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<uint32_t*>(&h);
+    } else {
+        __half2 h = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<uint32_t*>(&h);
+    }
+}
+
+// 32 columns [32 h, 32 h + 32) of this thread's P row: kernel values, packed
+// in pairs, stored as four 16-byte chunks of the swizzled K-major layout.
+template <int KIND, int BF16>
+__device__ __forceinline__ void tp_chunk(const uint32_t (&r)[32], int h, int row, bool dtile, uint32_t prow,
+                                         uint32_t nsw) {
+    uint32_t pk[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        float k0 = kernel_from_s<KIND>(__uint_as_float(r[2 * e]));
+        float k1 = kernel_from_s<KIND>(__uint_as_float(r[2 * e + 1]));
+        if constexpr (KIND == GP_KERNEL_MATERN12) {
+            if (dtile) {
+                const int col = h * 32 + 2 * e;
+                if (col == row) k0 = 0.0f;
+                if (col + 1 == row) k1 = 0.0f;
+            }
+        }
+        pk[e] = pack2<BF16>(k0, k1);
+    }
+    const uint32_t kb = prow + (uint32_t)(h >> 1) * kPKBlock;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t c = (uint32_t)((h & 1) * 4 + q);
+        st_shared_v4(kb + ((c ^ nsw) << 4), pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+    }
+}
+
+template <int KIND, int BF16>
+__device__ void tp_epilogue(const TpParams& p, TpBarriers& bars, const uint8_t* sP, uint32_t tmem, int wg, int wq,
+                            int lane) {
+    const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
+    const int row = wq * 32 + lane;                  // row within this warpgroup's tile
+    const uint32_t nrow = (uint32_t)(wg * kBM + row); // row of the P operand (0..255)
+    const uint32_t nsw = nrow & 7u;
+    const uint32_t aP = ptx::smem_u32(sP) + nrow * 128u;
+    uint32_t gt = 0;
+    int ic = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < p.n_items; item += gridDim.x, ++ic) {
+        int ip, sp, j0, j1;
+        item_range(p, item, ip, sp, j0, j1);
+        const uint32_t T = (uint32_t)(j1 - j0);
+        const int it = 2 * ip + wg;   // this warpgroup's row tile
+        for (uint32_t t = 0; t < T; ++t) {
+            const uint32_t g = gt + t, pb = g & 1;
+            if (!ptx::mbar_wait(&bars.s_full[wg], g & 1, p.limit_ns)) { ok = false; break; }
+            ptx::tc_fence_after();
+            const uint32_t tS = tmem + lane_off + (uint32_t)wg * 128u;
+            const bool dtile = (KIND == GP_KERNEL_MATERN12) && p.diag && (j0 + (int)t == it);
+            const uint32_t prow = aP + pb * kPBytes;
+            uint32_t ra[32], rb[32];
+            ptx::tmem_ld32(tS, ra);
+            ptx::tmem_ld32(tS + 32u, rb);
+            ptx::tmem_wait_ld();
+            ptx::tmem_reg_fence(ra);
+            ptx::tmem_reg_fence(rb);
+            if (g >= 2) {   // the value product that last read this P buffer is done
+                if (!ptx::mbar_wait(&bars.p_empty[pb], ((g >> 1) - 1) & 1, p.limit_ns)) { ok = false; break; }
+            }
+            tp_chunk<KIND, BF16>(ra, 0, row, dtile, prow, nsw);
+            tp_chunk<KIND, BF16>(rb, 1, row, dtile, prow, nsw);
+            ptx::tmem_ld32(tS + 64u, ra);
+            ptx::tmem_ld32(tS + 96u, rb);
+            ptx::tmem_wait_ld();
+            ptx::tmem_reg_fence(ra);
+            ptx::tmem_reg_fence(rb);
+            ptx::tc_fence_before();
+            ptx::mbar_arrive(&bars.s_empty[wg]);   // the MMA may overwrite this S buffer now
+            tp_chunk<KIND, BF16>(ra, 2, row, dtile, prow, nsw);
+            tp_chunk<KIND, BF16>(rb, 3, row, dtile, prow, nsw);
+            ptx::fence_proxy_async_smem();        // P stores -> visible to the tensor core
+            ptx::mbar_arrive(&bars.p_full[pb]);
+        }
+        if (!ok) break;
+        // O^T read-out: lanes [0, rv) are the rows of Vt; columns of this row tile.
+        if (!ptx::mbar_wait(&bars.o_full, ic & 1, p.limit_ns)) { ok = false; break; }
+        ptx::tc_fence_after();
+        if (wq * 32 < p.rv) {   // warp-uniform
+            const int r = wq * 32 + lane;
+            float* dst = p.partial + ((int64_t)sp * p.rv + r) * p.ld_part + (int64_t)ip * kPairRows + wg * kBM;
+            for (int h = 0; h < 4; ++h) {
+                uint32_t o[32];
+                ptx::tmem_ld32(tmem + lane_off + kTmemO + (uint32_t)(wg * kBM + h * 32), o);
+                ptx::tmem_wait_ld();
+                ptx::tmem_reg_fence(o);
+                float4* d4 = reinterpret_cast<float4*>(dst + h * 32);
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    d4[q] = make_float4(__uint_as_float(o[4 * q]), __uint_as_float(o[4 * q + 1]),
+                                        __uint_as_float(o[4 * q + 2]), __uint_as_float(o[4 * q + 3]));
+            }
+        }
+        ptx::tc_fence_before();
+        ptx::mbar_arrive(&bars.o_empty);
+        gt += T;
+    }
+    if (!ok) record_error(p.err, DEV_TIMEOUT);
+}
+
+struct TpSmem {
+    uint32_t xbytes, vtbytes, stage_bytes;
+    int stages, xi_bufs;
+    uint32_t total;   // dynamic shared memory to request (includes 1 KB alignment slack)
+};
+
+__host__ __device__ inline TpSmem tp_smem(int k_pad, int rv) {
+    TpSmem m;
+    m.xbytes = (uint32_t)kBM * (uint32_t)k_pad * 2u;
+    m.vtbytes = 2u * (uint32_t)rv * 128u;
+    m.stage_bytes = m.xbytes + m.vtbytes;
+    const uint32_t fixed = 1024u + 2u * kPBytes;
+    m.stages = 0;
+    m.xi_bufs = 2;
+    for (int xb = 2; xb >= 1 && m.stages < 3; --xb) {
+        const uint32_t xi = (uint32_t)xb * 2u * m.xbytes;
+        int st = 0;
+        for (int s = kMaxStages; s >= 2; --s)
+            if (fixed + xi + (uint32_t)s * m.stage_bytes <= (uint32_t)kMaxSmemBytes - 512u) { st = s; break; }
+        if (st > m.stages) { m.stages = st; m.xi_bufs = xb; }
+    }
+    m.total = fixed + (uint32_t)m.xi_bufs * 2u * m.xbytes + (uint32_t)m.stages * m.stage_bytes;
+    return m;
+}
+
+template <int KIND, int BF16>
+__global__ void __launch_bounds__(kThreads, 1)
+kmvm_tp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const __grid_constant__ CUtensorMap tmV, const TpParams p) {
+    extern __shared__ uint8_t dsm[];
+    __shared__ TpBarriers bars;
+    __shared__ uint32_t tmem_slot;
+
+    uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
+    const TpSmem m = tp_smem(p.k_pad, p.rv);
+    uint8_t* sSt = base;
+    uint8_t* sP = base + (uint32_t)p.stages * m.stage_bytes;
+    uint8_t* sXi = sP + 2u * kPBytes;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kMaxStages; ++s) {
+            ptx::mbar_init(&bars.full[s], 1);
+            ptx::mbar_init(&bars.empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            ptx::mbar_init(&bars.s_full[b], 1);
+            ptx::mbar_init(&bars.s_empty[b], 128);
+            ptx::mbar_init(&bars.p_full[b], 256);
+            ptx::mbar_init(&bars.p_empty[b], 1);
+            ptx::mbar_init(&bars.xi_full[b], 1);
+            ptx::mbar_init(&bars.xi_empty[b], 1);
+        }
+        ptx::mbar_init(&bars.o_full, 1);
+        ptx::mbar_init(&bars.o_empty, 256);
+        ptx::mbar_init(&bars.drain, 1);
+        ptx::fence_mbar_init();
+    }
+    if (warp == kTmaWarp && lane == 0) {
+        ptx::tma_prefetch_desc(&tmA);
+        ptx::tma_prefetch_desc(&tmB);
+        ptx::tma_prefetch_desc(&tmV);
+    }
+    if (warp == kMmaWarp) ptx::tmem_alloc(&tmem_slot, kTmemCols);
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == kTmaWarp) {
+        if (lane == 0) tp_producer(p, &tmA, &tmB, &tmV, bars, sSt, sXi, m.xbytes, m.vtbytes);
+        __syncwarp();
+    } else if (warp == kMmaWarp) {
+        if (lane == 0)
+            tp_mma(p, bars, sSt, sP, sXi, m.xbytes, m.vtbytes, tmem, ptx::idesc_f16(kBM, kBN, BF16),
+                   ptx::idesc_f16(kBM, kPairRows, BF16));
+        __syncwarp();
+    } else {
+        tp_epilogue<KIND, BF16>(p, bars, sP, tmem, warp >> 2, warp & 3, lane);
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    if (warp == kMmaWarp) ptx::tmem_dealloc(tmem, kTmemCols);
+}
+
+template <int KIND, int BF16>
+cudaError_t launch_tp_typed(const TcPlan& plan, const TpParams& prm, const CUtensorMap& a, const CUtensorMap& b,
+                            const CUtensorMap& v, cudaStream_t s) {
+    const TpSmem m = tp_smem(prm.k_pad, prm.rv);
+    auto kfn = kmvm_tp_kernel<KIND, BF16>;
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m.total);
+    if (e != cudaSuccess) return e;
+    kfn<<<plan.grid, kThreads, m.total, s>>>(a, b, v, prm);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tp_supported(int k_pad, int R_pad, int vsplit) {
+    const int rv = R_pad * (1 + vsplit);
+    return k_pad <= 64 && rv <= 128 && rv % 32 == 0 && tp_smem(k_pad, rv).stages >= 2;
+}
+
+TcPlan tp_plan(const Ctx* ctx, int64_t Nr, int64_t Nc, int R, int k_pad, int vsplit) {
+    TcPlan p;
+    p.engine = 1;
+    p.k_pad = k_pad;
+    p.R_pad = ((R + 15) / 16) * 16;
+    p.rv = p.R_pad * (1 + vsplit);
+    const int n_it = (int)((Nr + kBM - 1) / kBM);
+    p.n_it = (n_it + 1) / 2;                  // pairs of row tiles
+    p.n_jt = (int)((Nc + kBN - 1) / kBN);
+    p.Nr_pad = (int64_t)p.n_it * kPairRows;
+    p.Nc_pad = (int64_t)p.n_jt * kBN;
+    const int G = ctx->num_sms > 0 ? ctx->num_sms : 1;
+    // Column split minimising the busiest CTA's work (waves x tiles per item
+    // plus about two tiles of per-item cost) plus the reduction, which always
+    // runs here (it also sums the hi and lo rows).
+    int best = 1;
+    double best_cost = 1e300;
+    const int max_split = p.n_jt < 16 ? p.n_jt : 16;
+    for (int sp = 1; sp <= max_split; ++sp) {
+        const int64_t items = (int64_t)p.n_it * sp;
+        const int64_t waves = (items + G - 1) / G;
+        const int64_t tiles = (p.n_jt + sp - 1) / sp;
+        double cost = (double)waves * (double)(tiles + 2);
+        cost += 0.05 * (double)sp * (double)p.n_it * 2.0 * (double)p.rv / (double)G / 64.0;
+        if (cost < best_cost - 1e-9) { best_cost = cost; best = sp; }
+    }
+    p.n_split = best;
+    const int64_t items = (int64_t)p.n_it * p.n_split;
+    p.grid = (int)(items < G ? items : G);
+    return p;
+}
+
+size_t tp_partial_floats(const TcPlan& p) { return (size_t)p.n_split * p.rv * p.Nr_pad; }
+
+int launch_kmvm_tp(Ctx* ctx, const TcPlan& plan, const OperandLayout& L, const MvmArgs& a, const CUtensorMap& tmA,
+                   const CUtensorMap& tmB, const CUtensorMap& tmV, const float* outscale, float* partial,
+                   cudaStream_t s) {
+    TpParams prm;
+    prm.n_ip = plan.n_it;
+    prm.n_jt = plan.n_jt;
+    prm.n_split = plan.n_split;
+    prm.n_items = plan.n_it * plan.n_split;
+    prm.k_pad = plan.k_pad;
+    prm.rv = plan.rv;
+    const TpSmem m = tp_smem(plan.k_pad, plan.rv);
+    prm.stages = m.stages;
+    prm.xi_bufs = m.xi_bufs;
+    if (!tp_supported(plan.k_pad, plan.R_pad, plan.rv / plan.R_pad - 1)) return GP_ERR_UNSUPPORTED;
+    prm.diag = a.diag_coef != 0.0f ? 1 : 0;
+    prm.ld_part = plan.Nr_pad;
+    prm.partial = partial;
+    prm.err = ctx->dev_err;
+    prm.limit_ns = kWaitLimitNs;
+    const int bf = (L.prec == GP_PREC_BF16) ? 1 : 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    prof_begin(ctx, s);
+#define GPK_TP_CASE(K)                                                                                  \
+    case K:                                                                                             \
+        e = bf ? launch_tp_typed<K, 1>(plan, prm, tmA, tmB, tmV, s) : launch_tp_typed<K, 0>(plan, prm, tmA, tmB, tmV, s); \
+        break;
+    switch (a.kernel) {
+        GPK_TP_CASE(GP_KERNEL_RBF)
+        GPK_TP_CASE(GP_KERNEL_MATERN32)
+        GPK_TP_CASE(GP_KERNEL_MATERN12)
+        GPK_TP_CASE(GP_KERNEL_MATERN52)
+        default: return GP_ERR_INVALID;
+    }
+#undef GPK_TP_CASE
+    prof_end(ctx, s);
+    ctx->launches++;
+    if (e != cudaSuccess) return GP_ERR_CUDA;
+    // splits x {hi, lo} rows: partial[s][part * R_pad + c] = partial'[s * parts + part][c]
+    const int parts = plan.rv / plan.R_pad;
+    return launch_split_reduce(ctx, partial, plan.n_split * parts, plan.Nr_pad, a.Nr, a.R, plan.R_pad, outscale,
+                               0.0f, a.noise + a.diag_coef, a.Vnoise, a.Nc, a.out, a.ld_out, s);
+}
+
+}  // namespace gpk

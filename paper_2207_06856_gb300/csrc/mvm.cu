@@ -65,7 +65,8 @@ static void kop_layout(A& a, KOp& op, int64_t Nr, int64_t Nc, int R_max, bool sq
         a.template take<float>(64);
         a.template take<unsigned>(64);
         a.template take<unsigned>(128);
-        a.template take<float>((size_t)op.tp.n_split * rp * op.tp.Nr_pad);
+        a.template take<float>(op.tp.engine == 1 ? tp_partial_floats(op.tp)
+                                                  : (size_t)op.tp.n_split * rp * op.tp.Nr_pad);
     }
 }
 
@@ -94,11 +95,20 @@ static int kop_plan(const Ctx* ctx, KOp& op, const gp_hyp_t* hyp, int64_t Nr, in
         if (flags & GP_MVM_NO_XSPLIT) xsplit = 0;
         if (xsplit && make_layout(hyp->d, op.prec, 1, 0, 0).k_pad == 0) xsplit = 0;   // does not fit
         const int single = (flags & GP_MVM_BF16_SINGLE) ? 1 : 0;
-        const int vsplit = bf ? !single : ((flags & GP_MVM_VSPLIT) ? 1 : 0);
+        int vsplit = bf ? !single : ((flags & GP_MVM_VSPLIT) ? 1 : 0);
         const int psplit = bf ? !single : 0;
+        const int Rc = R < 64 ? R : 64;
+        const int Rp = ((Rc + 15) / 16) * 16;
+        const OperandLayout probe = make_layout(hyp->d, op.prec, xsplit, 1, psplit);
+        // Pair engine (transposed value product) unless the kernel tile is split
+        // or the operands do not fit its shared-memory plan.  There FP16 always
+        // carries v as hi + lo: the lo rows share the MMA's M dimension.
+        const bool pair = !(flags & GP_MVM_ONE_TILE) && !psplit && probe.k_pad != 0 &&
+                          tp_supported(probe.k_pad, Rp, bf ? 0 : 1);
+        if (pair && !bf) vsplit = 1;
         op.lay = make_layout(hyp->d, op.prec, xsplit, vsplit, psplit);
         if (op.lay.k_pad == 0) return GP_ERR_UNSUPPORTED;
-        op.tp = tc_plan(ctx, Nr, Nc, R < 64 ? R : 64, op.lay.k_pad);
+        op.tp = pair ? tp_plan(ctx, Nr, Nc, Rc, op.lay.k_pad, vsplit) : tc_plan(ctx, Nr, Nc, Rc, op.lay.k_pad);
     } else {
         return GP_ERR_INVALID;
     }
@@ -140,7 +150,8 @@ int kop_prepare(Ctx* ctx, WsCarver& wc, KOp& op, const gp_hyp_t* hyp, const floa
     op.outscale = wc.take<float>(64);
     op.cmax = wc.take<unsigned>(64);
     op.bbox = wc.take<unsigned>(128);
-    op.partial = wc.take<float>((size_t)op.tp.n_split * rp * op.tp.Nr_pad);
+    op.partial = wc.take<float>(op.tp.engine == 1 ? tp_partial_floats(op.tp)
+                                                  : (size_t)op.tp.n_split * rp * op.tp.Nr_pad);
     if (!wc.ok) return GP_ERR_WORKSPACE;
     GPK_TRY(launch_bbox(ctx, Xc, Nc, hyp->d, op.bbox, s));
     if (square) {
@@ -185,14 +196,23 @@ int kop_apply(Ctx* ctx, KOp& op, const float* V, int R, float* out, int64_t ld_o
         } else {
             TcPlan pl = op.tp;
             pl.R_pad = ((rc + 15) / 16) * 16;
+            if (pl.engine == 1) pl.rv = pl.R_pad * (op.lay.vsplit ? 2 : 1);
             GPK_TRY(launch_v_colmax(ctx, Vc, op.Nc, rc, op.cmax, s));
             GPK_TRY(launch_v_cast(ctx, op.prec, (op.flags & GP_MVM_SCALE_SQRT_N) ? 1 : 0, op.lay.vsplit, Vc, op.Nc,
                                   pl.Nc_pad, rc, pl.R_pad, op.cmax, op.a2, op.Vt, op.outscale, s));
             const CUtensorMapDataType dt =
                 op.prec == GP_PREC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-            GPK_TRY(encode_tmap_2d(&op.tmV, dt, op.Vt, pl.Nc_pad, (uint64_t)(op.lay.vsplit ? 2 : 1) * pl.R_pad,
-                                   pl.Nc_pad * 2, 64, pl.R_pad, CU_TENSOR_MAP_SWIZZLE_128B));
-            GPK_TRY(launch_kmvm_tc(ctx, pl, op.lay, a, op.tmA, op.tmB, op.tmV, op.outscale, op.partial, s));
+            const uint64_t vrows = (uint64_t)(op.lay.vsplit ? 2 : 1) * pl.R_pad;
+            if (pl.engine == 1) {
+                // one box carries the hi and lo rows of a 64-column K-block
+                GPK_TRY(encode_tmap_2d(&op.tmV, dt, op.Vt, pl.Nc_pad, vrows, pl.Nc_pad * 2, 64, (uint32_t)pl.rv,
+                                       CU_TENSOR_MAP_SWIZZLE_128B));
+                GPK_TRY(launch_kmvm_tp(ctx, pl, op.lay, a, op.tmA, op.tmB, op.tmV, op.outscale, op.partial, s));
+            } else {
+                GPK_TRY(encode_tmap_2d(&op.tmV, dt, op.Vt, pl.Nc_pad, vrows, pl.Nc_pad * 2, 64, pl.R_pad,
+                                       CU_TENSOR_MAP_SWIZZLE_128B));
+                GPK_TRY(launch_kmvm_tc(ctx, pl, op.lay, a, op.tmA, op.tmB, op.tmV, op.outscale, op.partial, s));
+            }
         }
     }
     return GP_OK;

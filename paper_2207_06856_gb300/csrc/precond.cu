@@ -240,36 +240,69 @@ wb_ltw_kernel(const float* __restrict__ L, int64_t N, int k, const float* __rest
     }
 }
 
-// One CTA, one warp per right-hand side: t = sum of partials (fixed order),
+// One warp per right-hand side: t = sum of partials (fixed order),
 // u = C^{-1} t with C = Lc Lc^T (forward then backward substitution, FP64).
-__global__ void wb_solve_kernel(const double* __restrict__ tpart, int nblk, int k, int R,
-                                const double* __restrict__ core, float* __restrict__ u_out,
-                                double* __restrict__ ybuf) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int e = threadIdx.x; e < k * R; e += blockDim.x) {
+// grid = ceil(R / 8) CTAs of 8 warps; CTA b solves columns 8b .. 8b+7.
+constexpr int kWbSolveWarps = 8;
+__global__ void __launch_bounds__(kWbSolveWarps * 32)
+wb_solve_kernel(const double* __restrict__ tpart, int nblk, int k, int R, const double* __restrict__ core,
+                float* __restrict__ u_out, double* __restrict__ ybuf) {
+    const int c0 = blockIdx.x * kWbSolveWarps;
+    const int nc = (R - c0) < kWbSolveWarps ? (R - c0) : kWbSolveWarps;
+    // t = sum over row blocks (fixed order) for this CTA's columns, layout [a][c]
+    for (int e = threadIdx.x; e < k * nc; e += blockDim.x) {
+        const int a = e / nc, c = c0 + e % nc;
         double t = 0.0;
-        for (int b = 0; b < nblk; ++b) t += tpart[(int64_t)b * k * R + e];
-        ybuf[e] = t;   // layout [a][c]
+        for (int b = 0; b < nblk; ++b) t += tpart[((int64_t)b * k + a) * R + c];
+        ybuf[a * R + c] = t;
     }
     __syncthreads();
-    for (int c = w; c < R; c += (blockDim.x >> 5)) {
-        // forward: Lc y = t
+    // One warp per right-hand side; lane l keeps rows a = l + 32 m in registers
+    // (k <= 512).  core holds Lc column-major: Lc(a, b) = core[b * k + a].
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int kMaxPer = 16;
+    if (w < nc) {
+        const int c = c0 + w;
+        double y[kMaxPer];
+#pragma unroll
+        for (int m = 0; m < kMaxPer; ++m) {
+            const int a = lane + 32 * m;
+            y[m] = a < k ? ybuf[a * R + c] : 0.0;
+        }
+        // forward, column-oriented: y_a /= Lc(a,a); y_i -= Lc(i,a) y_a for i > a
         for (int a = 0; a < k; ++a) {
-            double s = 0.0;
-            for (int j = lane; j < a; j += 32) s += core[(int64_t)j * k + a] * ybuf[j * R + c];
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) ybuf[a * R + c] = (ybuf[a * R + c] - s) / core[(int64_t)a * k + a];
-            __syncwarp();
+            const double* col = core + (int64_t)a * k;
+            double ya = 0.0;
+#pragma unroll
+            for (int m = 0; m < kMaxPer; ++m)
+                if (lane + 32 * m == a) ya = y[m] / col[a];
+            ya = __shfl_sync(0xffffffffu, ya, a & 31);
+#pragma unroll
+            for (int m = 0; m < kMaxPer; ++m) {
+                const int i = lane + 32 * m;
+                if (i == a) y[m] = ya;
+                else if (i > a && i < k) y[m] = fma(-col[i], ya, y[m]);
+            }
         }
-        // backward: Lc^T u = y
+        // backward, row-oriented: u_a = (y_a - sum_{j > a} Lc(j,a) u_j) / Lc(a,a)
         for (int a = k - 1; a >= 0; --a) {
-            double s = 0.0;
-            for (int j = a + 1 + lane; j < k; j += 32) s += core[(int64_t)a * k + j] * ybuf[j * R + c];
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) ybuf[a * R + c] = (ybuf[a * R + c] - s) / core[(int64_t)a * k + a];
-            __syncwarp();
+            const double* col = core + (int64_t)a * k;
+            double sacc = 0.0;
+#pragma unroll
+            for (int m = 0; m < kMaxPer; ++m) {
+                const int j = lane + 32 * m;
+                if (j > a && j < k) sacc = fma(col[j], y[m], sacc);
+            }
+            for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+#pragma unroll
+            for (int m = 0; m < kMaxPer; ++m)
+                if (lane + 32 * m == a) y[m] = (y[m] - sacc) / col[a];
         }
-        for (int a = lane; a < k; a += 32) u_out[a * R + c] = (float)ybuf[a * R + c];
+#pragma unroll
+        for (int m = 0; m < kMaxPer; ++m) {
+            const int a = lane + 32 * m;
+            if (a < k) u_out[a * R + c] = (float)y[m];
+        }
     }
 }
 
@@ -425,7 +458,8 @@ int woodbury_apply(Ctx* ctx, WsCarver& wc, const float* L, const double* core, i
     if (16 * R > 512) return GP_ERR_UNSUPPORTED;
     wb_ltw_kernel<<<(unsigned)nblk, 256, sh1, s>>>(L, N, k, W, R, active, rows_per, tpart);
     ctx->launches++;
-    wb_solve_kernel<<<1, 1024, 0, s>>>(tpart, (int)nblk, k, R, core, u, ybuf);
+    wb_solve_kernel<<<(unsigned)((R + kWbSolveWarps - 1) / kWbSolveWarps), kWbSolveWarps * 32, 0, s>>>(
+        tpart, (int)nblk, k, R, core, u, ybuf);
     ctx->launches++;
     const float inv_s2 = (float)(1.0 / noise), inv_s4 = (float)(1.0 / (noise * noise));
     int64_t g = (N + 255) / 256;

@@ -44,6 +44,7 @@ MVM_NO_XSPLIT = 0x400
 MVM_SCALE_SQRT_N = 0x800
 MVM_VSPLIT = 0x1000
 MVM_BF16_SINGLE = 0x2000
+MVM_ONE_TILE = 0x4000
 
 
 class GPKError(RuntimeError):

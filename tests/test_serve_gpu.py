@@ -138,7 +138,12 @@ def test_late_small_requests_overlap_a_large_one(gpk):
     """A large request is submitted first; small requests submitted while it
     runs are admitted and finish before it does (continuous batching, not a
     queue)."""
-    big = _requests(1, seed=13, n_min=150000, n_max=150001)[0]
+    # the large request is well conditioned (RBF, l = 1, sigma^2 = 0.05) so it
+    # converges in a few tens of iterations: the test is about overlap
+    big = workloads.Request(rid=0, arrival_s=0.0, X=(r := np.random.default_rng(13)).standard_normal(
+        (150000, 8)).astype(np.float32), y=np.zeros(150000, np.float32), Xstar=r.standard_normal((256, 8)).astype(
+        np.float32), kernel=0, lengthscale=np.ones(8, np.float32), outputscale=1.0, noise=0.05)
+    big.y[:] = np.sin(big.X.sum(axis=1)) + 0.1 * r.standard_normal(150000)
     small = _requests(4, seed=14, n_min=500, n_max=800)
     srv = gpk.Server(0, arena_bytes=4 << 30, max_slots=8, rank=20)
     try:
