@@ -338,7 +338,7 @@ def run_kmvm(args):
     X = torch.from_numpy(w.X).cuda()
     B = torch.from_numpy(w.rhs()).cuda()
     out = torch.empty_like(B)
-    fl = gpk.MVM_ONE_TILE if args.one_tile else 0
+    fl = (gpk.MVM_ONE_TILE if args.one_tile else 0) | (gpk.MVM_PSPLIT if args.psplit else 0)
     for _ in range(args.warmup):
         gpk.kmvm(ctx, hyp, X, B, precision=args.precision, add_noise=True, out=out, flags=fl)
     torch.cuda.synchronize()
@@ -356,7 +356,8 @@ def run_kmvm(args):
     ctx.check()
     pairs = float(w.N) ** 2
     print(json.dumps({"mode": "kmvm", "precision": args.precision, "kernel": args.kernel,
-                      "engine": "one-tile" if args.one_tile else "pair", "launches": n,
+                      "engine": "one-tile" if args.one_tile else "pair", "psplit": bool(args.psplit),
+                      "launches": n,
                       "avg_launch_ms": ms / max(n, 1), "pairs_per_s": pairs / (ms / max(n, 1) / 1e3)}), flush=True)
 
 
@@ -450,6 +451,7 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=152)
     ap.add_argument("--mode", default="solve", choices=["solve", "kmvm", "serve"])
     ap.add_argument("--one-tile", action="store_true", help="kmvm mode: the one-row-tile tensor-core engine")
+    ap.add_argument("--psplit", action="store_true", help="kmvm mode: FP16 kernel tile as hi + lo")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-arena-gb", type=float, default=48.0)

@@ -84,6 +84,10 @@ extern "C" {
 #define GP_MVM_BF16_SINGLE  0x2000  /* BF16: single-term kernel tile and v (faster,
                                        ~2^-8 rounding; the default carries both as
                                        hi + lo so the MVM meets 2e-3)             */
+#define GP_MVM_PSPLIT       0x8000  /* FP16: carry the kernel tile as hi + lo (22
+                                       bits; CG then needs about the FP32 iteration
+                                       count, at about 1.5x the MVM time).  BF16
+                                       does by default.                          */
 #define GP_MVM_ONE_TILE     0x4000  /* tensor-core MVM on the one-row-tile engine
                                        (P V with M = 128 rows, N = R) instead of
                                        the default pair engine (transposed

@@ -86,18 +86,22 @@ dots_kernel(const float* __restrict__ A, const float* __restrict__ B, int64_t N,
     if (active && !active[c]) return;
     const float* a = A + (int64_t)c * N;
     const float* b = B + (int64_t)c * N;
-    Lse acc{0.0, kEmptyExp};
-    double n2 = 0.0;
+    // Each thread's 8 products are exact in FP64 and summed there (no FP32
+    // product can overflow or underflow FP64); the (s, e) form starts at the
+    // thread partial, which saves the per-element exponent work.
+    double sp = 0.0, n2 = 0.0;
     const int64_t base = (int64_t)blockIdx.x * kDotChunk;
 #pragma unroll
     for (int q = 0; q < kDotPerThread; ++q) {
         const int64_t i = base + q * kDotThreads + threadIdx.x;
         if (i < N) {
             const double av = a[i], bv = b[i];
-            lse_add(acc, av * bv);
+            sp = fma(av, bv, sp);
             n2 = fma(av, av, n2);
         }
     }
+    Lse acc{0.0, kEmptyExp};
+    lse_add(acc, sp);
     for (int o = 16; o > 0; o >>= 1) {
         lse_merge(acc, lse_shfl(acc, o));
         n2 += __shfl_xor_sync(0xffffffffu, n2, o);
@@ -261,12 +265,14 @@ __global__ void update_d_kernel(float* __restrict__ d, const float* __restrict__
 }
 
 // gpart[(c * nblk + blk) * nb + j] = sum over the chunk of ZB_j[c][i] r[c][i]
-// (FP32 products summed per thread over its 8 elements, FP64 across threads).
+// (FP32 products summed over a warp's 256 elements, FP64 across warps and,
+// in gram_finalize_kernel, across blocks).  Dynamic shared memory: 8 x nb floats.
 __global__ void __launch_bounds__(kDotThreads)
 gram_kernel(const float* __restrict__ ZB, int nb, int R, const float* __restrict__ r, int64_t N, int nblk,
             const ColState* __restrict__ st, double* __restrict__ gpart) {
     const int c = blockIdx.y;
     if (!st[c].active) return;
+    extern __shared__ float sred[];   // [warp][j]
     const int64_t base = (int64_t)blockIdx.x * kDotChunk;
     float rv[kDotPerThread];
 #pragma unroll
@@ -274,7 +280,6 @@ gram_kernel(const float* __restrict__ ZB, int nb, int R, const float* __restrict
         const int64_t i = base + q * kDotThreads + threadIdx.x;
         rv[q] = i < N ? r[(int64_t)c * N + i] : 0.0f;
     }
-    __shared__ double sred[kDotThreads / 32];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     for (int j = 0; j < nb; ++j) {
         const float* zb = ZB + ((int64_t)j * R + c) * N;
@@ -284,16 +289,14 @@ gram_kernel(const float* __restrict__ ZB, int nb, int R, const float* __restrict
             const int64_t i = base + q * kDotThreads + threadIdx.x;
             if (i < N) a = fmaf(zb[i], rv[q], a);
         }
-        double v = a;
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (l == 0) sred[w] = v;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int q = 0; q < kDotThreads / 32; ++q) t += sred[q];
-            gpart[((int64_t)c * nblk + blockIdx.x) * nb + j] = t;
-        }
-        __syncthreads();
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (l == 0) sred[w * nb + j] = a;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+        double t = 0.0;
+        for (int q = 0; q < kDotThreads / 32; ++q) t += (double)sred[q * nb + j];
+        gpart[((int64_t)c * nblk + blockIdx.x) * nb + j] = t;
     }
 }
 
@@ -361,8 +364,8 @@ void cg_layout(A& a, const Ctx* ctx, int64_t N, int R, int rank, const gp_cg_opt
     a.template take<int>(4);
     a.template take<int>((size_t)R);
     a.template take<int>((size_t)R);
+    if (rank > 0) a.template take<double>((size_t)rank * rank);   // C^{-1}
     (void)ctx;
-    (void)rank;
 }
 
 int check_cg_args(const gp_hyp_t* hyp, int64_t N, int R, const gp_cg_opts_t* o) {
@@ -425,7 +428,8 @@ int CgSolver::precond(const float* W, float* Z, bool masked) {
         GPK_TRY(launched(1));
     }
     WsCarver wtmp = wc_rest;   // Woodbury scratch beyond the solver's buffers
-    return woodbury_apply(ctx, wtmp, pc.L, pc.core, rank, hyp.noise, N, W, R, masked ? b.aflags : nullptr, Z, s);
+    return woodbury_apply(ctx, wtmp, pc.L, pc.core, b.cinv, rank, hyp.noise, N, W, R, masked ? b.aflags : nullptr,
+                          Z, s);
 }
 
 int CgSolver::dots(const float* A, const float* Bv, bool masked) {
@@ -476,7 +480,8 @@ int CgSolver::iterate() {
         const int nb = k - nb0 + 1;   // basis vectors r_0 .. r_k of this run
         const float* ZB = reorth == GP_REORTH_PINV ? b.zeta : b.rho;
         for (int p = 0; p < passes; ++p) {
-            gram_kernel<<<gdot, kDotThreads, 0, s>>>(ZB, nb, R, b.r, N, b.nblk_dot, b.st, b.gpart);
+            gram_kernel<<<gdot, kDotThreads, (size_t)(kDotThreads / 32) * nb * sizeof(float), s>>>(
+                ZB, nb, R, b.r, N, b.nblk_dot, b.st, b.gpart);
             gram_finalize_kernel<<<(nb * R + 255) / 256, 256, 0, s>>>(b.gpart, b.nblk_dot, nb, R, b.st, b.coef);
             reorth_update_kernel<<<gcol, 256, 0, s>>>(b.rho, nb, R, b.coef, b.r, N, b.st);
             GPK_TRY(launched(3));
@@ -533,7 +538,9 @@ int CgSolver::setup(Ctx* c, WsCarver& wc, const gp_hyp_t* h, const float* X_, in
     b.nact = wc.take<int>(4);
     b.aflags = wc.take<int>((size_t)R);
     b.len0 = wc.take<int>((size_t)R);
+    b.cinv = rank > 0 ? wc.take<double>((size_t)rank * rank) : nullptr;
     if (!wc.ok) return GP_ERR_WORKSPACE;
+    if (rank > 0) GPK_TRY(woodbury_prepare(ctx, pc.core, rank, b.cinv, s));
     GPK_TRY(kop_prepare(ctx, wc, op, &hyp, X, N, X, N, R, o.precision, s));
     op_chk = &op;
     if (o.restarts > 0 && o.check_precision != (o.precision & 0xff)) {

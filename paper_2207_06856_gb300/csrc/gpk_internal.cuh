@@ -146,7 +146,7 @@ int launch_kmvm_tc(Ctx* ctx, const TcPlan& plan, const OperandLayout& L, const M
 
 // Tensor-core engine with the transposed value product (kmvm_tp.cu).  n_it
 // counts pairs of 128-row tiles; the partial buffer is always used.
-bool tp_supported(int k_pad, int R_pad, int vsplit);
+bool tp_supported(int k_pad, int R_pad, int vsplit, int psplit);
 TcPlan tp_plan(const Ctx* ctx, int64_t Nr, int64_t Nc, int R, int k_pad, int vsplit);
 size_t tp_partial_floats(const TcPlan& p);
 int launch_kmvm_tp(Ctx* ctx, const TcPlan& plan, const OperandLayout& L, const MvmArgs& a, const CUtensorMap& tmA,
@@ -209,9 +209,12 @@ size_t pivchol_workspace(const Ctx* ctx, int64_t N, int d, int rank);
 int pivchol_run(Ctx* ctx, WsCarver& wc, const gp_hyp_t* hyp, const float* X, int64_t N, int rank, float* L,
                 int32_t* piv, double* core, int* rank_out_host, cudaStream_t s);
 size_t woodbury_workspace(const Ctx* ctx, int64_t N, int k, int R);
-// Z = P^{-1} W on the active columns (active may be null = all).
-int woodbury_apply(Ctx* ctx, WsCarver& wc, const float* L, const double* core, int k, double noise, int64_t N,
-                   const float* W, int R, const int* active, float* Z, cudaStream_t s);
+// cinv (k x k FP64) = C^{-1} from the core factor, once per preconditioner use.
+int woodbury_prepare(Ctx* ctx, const double* core, int k, double* cinv, cudaStream_t s);
+// Z = P^{-1} W on the active columns (active may be null = all).  cinv from
+// woodbury_prepare, or null to form it in the call's own scratch.
+int woodbury_apply(Ctx* ctx, WsCarver& wc, const float* L, const double* core, const double* cinv, int k,
+                   double noise, int64_t N, const float* W, int R, const int* active, float* Z, cudaStream_t s);
 
 // ---- solver (cg.cu), backward (vjp.cu), loss (mll.cu) ----
 size_t cg_workspace(const Ctx* ctx, const gp_hyp_t* hyp, int64_t N, int R, int rank, const gp_cg_opts_t* o);
@@ -236,6 +239,7 @@ struct CgBufs {
     int* nact;
     int* aflags;
     int* len0;   // per-column iterations of the first (unrestarted) run
+    double* cinv;  // C^{-1} of the Woodbury core (rank > 0)
     int nb_max, nblk_dot;
 };
 

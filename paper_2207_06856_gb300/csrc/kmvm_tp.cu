@@ -18,13 +18,24 @@
 // costs no extra instruction.  P is the B operand and therefore lives in
 // shared memory: each epilogue thread writes its row of P as 16-byte chunks in
 // the 128-byte-swizzled K-major layout the MMA reads (chunk c of row n at
-// physical chunk c ^ (n mod 8)), then fences to the async proxy.
+// physical chunk c ^ (n mod 8)), then fences to the async proxy.  With
+// PSPLIT the kernel tile is carried as hi + lo (Veltkamp split in FP32 on the
+// FMA pipe: hi keeps the operand format's significand, lo = k - hi exactly
+// before its own rounding), and each K-block is multiplied twice.
 //
-// Work item = (pair of 128-row tiles, column split).  Warps: 0-3 epilogue of
-// row tile 0, 4-7 epilogue of row tile 1, 8 TMA producer, 9 MMA issuer and
-// TMEM owner.  TMEM: S of tile 0 [0,128), S of tile 1 [128,256), O^T
-// [256,512).  Shared memory: the X_j / Vt_j stage ring first, then two P
-// buffers of 64 KB, then the row-tile buffers.  The A operand of the value
+// Single-term P is double-buffered per tile (two 64 KB buffers) and its value
+// product issued once the whole tile is stored, so the next tile's S product,
+// issued as soon as the epilogue has read S, never queues behind it.  The
+// hi + lo tile needs twice the bytes: it is staged per 64-column K-block (two
+// 64 KB buffers) and each K-block's product is issued as soon as it is stored.
+//
+// Work item = (pair of 128-row tiles, column split).  Warps: 0-15 epilogue
+// (warpgroup q handles row tile q & 1, columns [64 (q >> 1), 64 (q >> 1) + 64):
+// four warps per scheduler hide the TMEM and shared-memory latencies behind the
+// special-function work), 16 TMA producer, 17 MMA issuer and TMEM owner.  TMEM: S of tile 0 [0,128), S of tile 1 [128,256), O^T
+// [256,512).  Shared memory: the X_j / Vt_j stage ring first, then the two
+// K-block P buffers (32 KB each, 64 KB with the hi + lo split), then the
+// row-tile buffers.  The A operand of the value
 // product spans 128 rows of which the first rv = R_pad (1 + vsplit) hold Vt;
 // the rest reads the following shared memory (the next K-block, stage or P
 // buffer: always inside the allocation) and lands in accumulator rows that
@@ -46,19 +57,20 @@ constexpr int kBM = 128;
 constexpr int kBN = 128;
 constexpr int kPairRows = 256;
 constexpr int kMaxStages = 6;
-constexpr int kThreads = 320;
-constexpr int kTmaWarp = 8;
-constexpr int kMmaWarp = 9;
+constexpr int kEpiWarps = 16;
+constexpr int kThreads = (kEpiWarps + 2) * 32;
+constexpr int kTmaWarp = kEpiWarps;
+constexpr int kMmaWarp = kEpiWarps + 1;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kTmemO = 256;
 constexpr uint32_t kPKBlock = (uint32_t)kPairRows * 128u;   // one 64-column K-block of P: 256 rows x 128 B
-constexpr uint32_t kPBytes = 2u * kPKBlock;                  // one P buffer (128 columns)
 constexpr int kMaxSmemBytes = 227 * 1024;   // opt-in maximum per CTA (512 B kept for static shared memory)
 
 struct TpParams {
     int n_ip, n_jt, n_split, n_items;
     int k_pad, rv;        // rv: rows of Vt per tile (R_pad, or 2 R_pad with the hi + lo split)
     int stages, xi_bufs;
+    int psplit;           // 1: P carried as hi + lo
     int diag;             // square Matern-1/2 operator: P_ii = 0 on chip (exact diagonal added later)
     int64_t ld_part;      // n_ip * 256
     float* partial;       // [n_split][rv][ld_part]
@@ -71,7 +83,7 @@ struct TpBarriers {
     uint64_t empty[kMaxStages];
     uint64_t s_full[2];     // per row tile (epilogue warpgroup)
     uint64_t s_empty[2];
-    uint64_t p_full[2];     // per P buffer
+    uint64_t p_full[2];     // per P buffer: tile slot (single P) or K-block (hi + lo P)
     uint64_t p_empty[2];
     uint64_t o_full;
     uint64_t o_empty;
@@ -139,8 +151,10 @@ __device__ void tp_producer(const TpParams& p, const CUtensorMap* tmA, const CUt
 
 // ---- MMA issuer (one thread) ----------------------------------------------------
 // Event driven: S(t) for both row tiles once their S buffers have been read
-// and the stage has landed; the value product of tile t once both halves of
-// P(t) are in shared memory (and, first in an item, O has been read out).
+// and the stage has landed; the value product of K-block kb of tile t once
+// both row tiles' P columns of that K-block are in shared memory (and, first
+// in an item, O has been read out).
+template <int PSPLIT>
 __device__ void tp_mma(const TpParams& p, TpBarriers& bars, const uint8_t* sSt, const uint8_t* sP,
                        const uint8_t* sXi, uint32_t xbytes, uint32_t vtbytes, uint32_t tmem, uint32_t id_s,
                        uint32_t id_pv) {
@@ -167,7 +181,7 @@ __device__ void tp_mma(const TpParams& p, TpBarriers& bars, const uint8_t* sSt, 
         if (!ptx::mbar_wait(&bars.xi_full[xb], use & 1, p.limit_ns)) { ok = false; break; }
         ptx::tc_fence_after();
         const uint32_t aXi = ptx::smem_u32(sXi) + (uint32_t)xb * 2u * xbytes;
-        uint32_t ts = 0, tp = 0;
+        uint32_t ts = 0, tp = 0, tk = 0;
         long long idle_since = clock64();
         while (tp < T) {
             bool progressed = false;
@@ -192,24 +206,33 @@ __device__ void tp_mma(const TpParams& p, TpBarriers& bars, const uint8_t* sSt, 
                     progressed = true;
                 }
             }
+            // value product of tile tp: whole tile (single P) or K-block tk (hi + lo P)
             if (tp < ts) {
-                const uint32_t g = gt + tp, pb = g & 1;
-                const bool o_free = (tp > 0) || (ic == 0) || ptx::mbar_test(&bars.o_empty, (ic - 1) & 1);
-                if (o_free && ptx::mbar_test(&bars.p_full[pb], (g >> 1) & 1)) {
+                const uint32_t g = gt + tp;
+                const uint32_t kb = PSPLIT ? tk : 0u;
+                const uint32_t buf = PSPLIT ? kb : (g & 1u);
+                const uint32_t par = PSPLIT ? (g & 1u) : ((g >> 1) & 1u);
+                const bool o_free = (tp > 0) || (kb > 0) || (ic == 0) || ptx::mbar_test(&bars.o_empty, (ic - 1) & 1);
+                if (o_free && ptx::mbar_test(&bars.p_full[buf], par)) {
                     ptx::tc_fence_after();
                     const uint32_t st = (n + tp) % S;
-                    const uint32_t aV = aSt + st * stage_bytes + xbytes;
-                    const uint32_t aPb = aP + pb * kPBytes;
+                    const uint32_t aV = aSt + st * stage_bytes + xbytes + kb * kblk;
+                    const uint32_t aPb = aP + buf * 2u * kPKBlock;
+                    // single P: K-blocks 0, 1 of the tile (8 steps); hi + lo: hi then lo of K-block kb
 #pragma unroll
-                    for (int kk = 0; kk < kBN / 16; ++kk) {
-                        const uint32_t kb = (uint32_t)(kk >> 2), ko = (uint32_t)(kk & 3) * 32u;
-                        ptx::mma_f16_ss(tmem + kTmemO, ptx::smem_desc_at(hi_128, aV + kb * kblk + ko),
-                                        ptx::smem_desc_at(hi_128, aPb + kb * kPKBlock + ko), id_pv,
-                                        (tp > 0 || kk > 0) ? 1u : 0u);
+                    for (int q = 0; q < 8; ++q) {
+                        const uint32_t kk = (uint32_t)(q & 3) * 32u, hq = (uint32_t)(q >> 2);
+                        const uint32_t aVq = PSPLIT ? aV + kk : aV + hq * kblk + kk;
+                        const uint32_t aPq = aPb + hq * kPKBlock + kk;
+                        ptx::mma_f16_ss(tmem + kTmemO, ptx::smem_desc_at(hi_128, aVq), ptx::smem_desc_at(hi_128, aPq),
+                                        id_pv, (tp > 0 || kb > 0 || q > 0) ? 1u : 0u);
                     }
-                    ptx::mma_commit(&bars.empty[st]);    // X_j and Vt_j of this stage are consumed
-                    ptx::mma_commit(&bars.p_empty[pb]);  // P buffer pb may be rewritten
-                    ++tp;
+                    ptx::mma_commit(&bars.p_empty[buf]);      // this P buffer may be rewritten
+                    if (!PSPLIT || kb == 1) {
+                        ptx::mma_commit(&bars.empty[st]);     // X_j and Vt_j of this stage are consumed
+                        ++tp;
+                    }
+                    if (PSPLIT) tk = kb ^ 1u;
                     progressed = true;
                 }
             }
@@ -245,11 +268,15 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
 }
 
 // 32 columns [32 h, 32 h + 32) of this thread's P row: kernel values, packed
-// in pairs, stored as four 16-byte chunks of the swizzled K-major layout.
-template <int KIND, int BF16>
-__device__ __forceinline__ void tp_chunk(const uint32_t (&r)[32], int h, int row, bool dtile, uint32_t prow,
+// in pairs (and, with PSPLIT, split hi + lo first), stored as four 16-byte
+// chunks of the swizzled K-major layout of K-block buffer pkb.
+template <int KIND, int BF16, int PSPLIT>
+__device__ __forceinline__ void tp_chunk(const uint32_t (&r)[32], int h, int row, bool dtile, uint32_t pkb,
                                          uint32_t nsw) {
+    // Veltkamp factor 2^(24 - t) + 1 leaves t significant bits in hi: 11 (FP16) or 8 (BF16)
+    constexpr float kSplit = BF16 ? 65537.0f : 8193.0f;
     uint32_t pk[16];
+    uint32_t pl[PSPLIT ? 16 : 1];
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
         float k0 = kernel_from_s<KIND>(__uint_as_float(r[2 * e]));
@@ -261,24 +288,35 @@ __device__ __forceinline__ void tp_chunk(const uint32_t (&r)[32], int h, int row
                 if (col + 1 == row) k1 = 0.0f;
             }
         }
-        pk[e] = pack2<BF16>(k0, k1);
+        if constexpr (PSPLIT) {
+            // explicit round-to-nearest operations: no contraction into FMAs
+            const float c0 = __fmul_rn(k0, kSplit), c1 = __fmul_rn(k1, kSplit);
+            const float h0 = __fsub_rn(c0, __fsub_rn(c0, k0)), h1 = __fsub_rn(c1, __fsub_rn(c1, k1));
+            pk[e] = pack2<BF16>(h0, h1);
+            pl[e] = pack2<BF16>(__fsub_rn(k0, h0), __fsub_rn(k1, h1));
+        } else {
+            pk[e] = pack2<BF16>(k0, k1);
+        }
     }
-    const uint32_t kb = prow + (uint32_t)(h >> 1) * kPKBlock;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const uint32_t c = (uint32_t)((h & 1) * 4 + q);
-        st_shared_v4(kb + ((c ^ nsw) << 4), pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+        const uint32_t off = (c ^ nsw) << 4;
+        st_shared_v4(pkb + off, pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+        if constexpr (PSPLIT) st_shared_v4(pkb + kPKBlock + off, pl[4 * q], pl[4 * q + 1], pl[4 * q + 2], pl[4 * q + 3]);
     }
 }
 
-template <int KIND, int BF16>
+template <int KIND, int BF16, int PSPLIT>
 __device__ void tp_epilogue(const TpParams& p, TpBarriers& bars, const uint8_t* sP, uint32_t tmem, int wg, int wq,
                             int lane) {
+    const int tl = wg & 1, ch = wg >> 1;              // row tile of the pair, column half (= K-block)
     const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
-    const int row = wq * 32 + lane;                  // row within this warpgroup's tile
-    const uint32_t nrow = (uint32_t)(wg * kBM + row); // row of the P operand (0..255)
+    const int row = wq * 32 + lane;                   // row within the tile
+    const uint32_t nrow = (uint32_t)(tl * kBM + row); // row of the P operand (0..255)
     const uint32_t nsw = nrow & 7u;
-    const uint32_t aP = ptx::smem_u32(sP) + nrow * 128u;
+    // P buffers are 64 KB: single P: [tile slot][K-block]; hi + lo: [K-block][hi, lo]
+    const uint32_t aProw = ptx::smem_u32(sP) + nrow * 128u;
     uint32_t gt = 0;
     int ic = 0;
     bool ok = true;
@@ -286,47 +324,48 @@ __device__ void tp_epilogue(const TpParams& p, TpBarriers& bars, const uint8_t* 
         int ip, sp, j0, j1;
         item_range(p, item, ip, sp, j0, j1);
         const uint32_t T = (uint32_t)(j1 - j0);
-        const int it = 2 * ip + wg;   // this warpgroup's row tile
+        const int it = 2 * ip + tl;   // this warpgroup's row tile
         for (uint32_t t = 0; t < T; ++t) {
-            const uint32_t g = gt + t, pb = g & 1;
-            if (!ptx::mbar_wait(&bars.s_full[wg], g & 1, p.limit_ns)) { ok = false; break; }
+            const uint32_t g = gt + t;
+            if (!ptx::mbar_wait(&bars.s_full[tl], g & 1, p.limit_ns)) { ok = false; break; }
             ptx::tc_fence_after();
-            const uint32_t tS = tmem + lane_off + (uint32_t)wg * 128u;
+            const uint32_t tS = tmem + lane_off + (uint32_t)tl * 128u + (uint32_t)ch * 64u;
             const bool dtile = (KIND == GP_KERNEL_MATERN12) && p.diag && (j0 + (int)t == it);
-            const uint32_t prow = aP + pb * kPBytes;
             uint32_t ra[32], rb[32];
             ptx::tmem_ld32(tS, ra);
             ptx::tmem_ld32(tS + 32u, rb);
             ptx::tmem_wait_ld();
             ptx::tmem_reg_fence(ra);
             ptx::tmem_reg_fence(rb);
-            if (g >= 2) {   // the value product that last read this P buffer is done
-                if (!ptx::mbar_wait(&bars.p_empty[pb], ((g >> 1) - 1) & 1, p.limit_ns)) { ok = false; break; }
-            }
-            tp_chunk<KIND, BF16>(ra, 0, row, dtile, prow, nsw);
-            tp_chunk<KIND, BF16>(rb, 1, row, dtile, prow, nsw);
-            ptx::tmem_ld32(tS + 64u, ra);
-            ptx::tmem_ld32(tS + 96u, rb);
-            ptx::tmem_wait_ld();
-            ptx::tmem_reg_fence(ra);
-            ptx::tmem_reg_fence(rb);
             ptx::tc_fence_before();
-            ptx::mbar_arrive(&bars.s_empty[wg]);   // the MMA may overwrite this S buffer now
-            tp_chunk<KIND, BF16>(ra, 2, row, dtile, prow, nsw);
-            tp_chunk<KIND, BF16>(rb, 3, row, dtile, prow, nsw);
+            ptx::mbar_arrive(&bars.s_empty[tl]);   // this half of S is in registers
+            uint32_t buf;
+            if constexpr (PSPLIT) {
+                // K-block buffer ch is free once the previous tile's product of it is done
+                buf = (uint32_t)ch;
+                if (g >= 1 && !ptx::mbar_wait(&bars.p_empty[buf], (g - 1) & 1, p.limit_ns)) { ok = false; break; }
+            } else {
+                // tile slot g & 1 is free once the product of tile g - 2 is done
+                buf = g & 1u;
+                if (g >= 2 && !ptx::mbar_wait(&bars.p_empty[buf], ((g >> 1) - 1) & 1, p.limit_ns)) { ok = false; break; }
+            }
+            const uint32_t pkb = aProw + buf * 2u * kPKBlock + (PSPLIT ? 0u : (uint32_t)ch * kPKBlock);
+            tp_chunk<KIND, BF16, PSPLIT>(ra, 2 * ch, row, dtile, pkb, nsw);
+            tp_chunk<KIND, BF16, PSPLIT>(rb, 2 * ch + 1, row, dtile, pkb, nsw);
             ptx::fence_proxy_async_smem();        // P stores -> visible to the tensor core
-            ptx::mbar_arrive(&bars.p_full[pb]);
+            ptx::mbar_arrive(&bars.p_full[buf]);
         }
         if (!ok) break;
-        // O^T read-out: lanes [0, rv) are the rows of Vt; columns of this row tile.
+        if (!ok) break;
+        // O^T read-out: lanes [0, rv) are the rows of Vt; this warpgroup's 64 columns.
         if (!ptx::mbar_wait(&bars.o_full, ic & 1, p.limit_ns)) { ok = false; break; }
         ptx::tc_fence_after();
         if (wq * 32 < p.rv) {   // warp-uniform
             const int r = wq * 32 + lane;
-            float* dst = p.partial + ((int64_t)sp * p.rv + r) * p.ld_part + (int64_t)ip * kPairRows + wg * kBM;
-            for (int h = 0; h < 4; ++h) {
+            float* dst = p.partial + ((int64_t)sp * p.rv + r) * p.ld_part + (int64_t)ip * kPairRows + tl * kBM + ch * 64;
+            for (int h = 0; h < 2; ++h) {
                 uint32_t o[32];
-                ptx::tmem_ld32(tmem + lane_off + kTmemO + (uint32_t)(wg * kBM + h * 32), o);
+                ptx::tmem_ld32(tmem + lane_off + kTmemO + (uint32_t)(tl * kBM + ch * 64 + h * 32), o);
                 ptx::tmem_wait_ld();
                 ptx::tmem_reg_fence(o);
                 float4* d4 = reinterpret_cast<float4*>(dst + h * 32);
@@ -344,17 +383,18 @@ __device__ void tp_epilogue(const TpParams& p, TpBarriers& bars, const uint8_t* 
 }
 
 struct TpSmem {
-    uint32_t xbytes, vtbytes, stage_bytes;
+    uint32_t xbytes, vtbytes, stage_bytes, pbuf;
     int stages, xi_bufs;
     uint32_t total;   // dynamic shared memory to request (includes 1 KB alignment slack)
 };
 
-__host__ __device__ inline TpSmem tp_smem(int k_pad, int rv) {
+__host__ __device__ inline TpSmem tp_smem(int k_pad, int rv, int psplit) {
     TpSmem m;
     m.xbytes = (uint32_t)kBM * (uint32_t)k_pad * 2u;
     m.vtbytes = 2u * (uint32_t)rv * 128u;
     m.stage_bytes = m.xbytes + m.vtbytes;
-    const uint32_t fixed = 1024u + 2u * kPBytes;
+    m.pbuf = (uint32_t)(1 + psplit) * kPKBlock;
+    const uint32_t fixed = 1024u + 4u * kPKBlock;   // two 64 KB P buffers
     m.stages = 0;
     m.xi_bufs = 2;
     for (int xb = 2; xb >= 1 && m.stages < 3; --xb) {
@@ -368,7 +408,7 @@ __host__ __device__ inline TpSmem tp_smem(int k_pad, int rv) {
     return m;
 }
 
-template <int KIND, int BF16>
+template <int KIND, int BF16, int PSPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
 kmvm_tp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmV, const TpParams p) {
@@ -377,10 +417,10 @@ kmvm_tp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     __shared__ uint32_t tmem_slot;
 
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
-    const TpSmem m = tp_smem(p.k_pad, p.rv);
+    const TpSmem m = tp_smem(p.k_pad, p.rv, PSPLIT);
     uint8_t* sSt = base;
     uint8_t* sP = base + (uint32_t)p.stages * m.stage_bytes;
-    uint8_t* sXi = sP + 2u * kPBytes;
+    uint8_t* sXi = sP + 4u * kPKBlock;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -390,14 +430,14 @@ kmvm_tp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
         for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(&bars.s_full[b], 1);
-            ptx::mbar_init(&bars.s_empty[b], 128);
-            ptx::mbar_init(&bars.p_full[b], 256);
-            ptx::mbar_init(&bars.p_empty[b], 1);
+            ptx::mbar_init(&bars.s_empty[b], 256);              // the two warpgroups of a row tile
             ptx::mbar_init(&bars.xi_full[b], 1);
             ptx::mbar_init(&bars.xi_empty[b], 1);
+            ptx::mbar_init(&bars.p_full[b], PSPLIT ? 256 : 512); // K-block: 2 warpgroups; tile: all 4
+            ptx::mbar_init(&bars.p_empty[b], 1);
         }
         ptx::mbar_init(&bars.o_full, 1);
-        ptx::mbar_init(&bars.o_empty, 256);
+        ptx::mbar_init(&bars.o_empty, kEpiWarps * 32);
         ptx::mbar_init(&bars.drain, 1);
         ptx::fence_mbar_init();
     }
@@ -417,11 +457,11 @@ kmvm_tp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         __syncwarp();
     } else if (warp == kMmaWarp) {
         if (lane == 0)
-            tp_mma(p, bars, sSt, sP, sXi, m.xbytes, m.vtbytes, tmem, ptx::idesc_f16(kBM, kBN, BF16),
+            tp_mma<PSPLIT>(p, bars, sSt, sP, sXi, m.xbytes, m.vtbytes, tmem, ptx::idesc_f16(kBM, kBN, BF16),
                    ptx::idesc_f16(kBM, kPairRows, BF16));
         __syncwarp();
     } else {
-        tp_epilogue<KIND, BF16>(p, bars, sP, tmem, warp >> 2, warp & 3, lane);
+        tp_epilogue<KIND, BF16, PSPLIT>(p, bars, sP, tmem, warp >> 2, warp & 3, lane);
     }
     ptx::tc_fence_before();
     __syncthreads();
@@ -429,11 +469,11 @@ kmvm_tp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     if (warp == kMmaWarp) ptx::tmem_dealloc(tmem, kTmemCols);
 }
 
-template <int KIND, int BF16>
+template <int KIND, int BF16, int PSPLIT>
 cudaError_t launch_tp_typed(const TcPlan& plan, const TpParams& prm, const CUtensorMap& a, const CUtensorMap& b,
                             const CUtensorMap& v, cudaStream_t s) {
-    const TpSmem m = tp_smem(prm.k_pad, prm.rv);
-    auto kfn = kmvm_tp_kernel<KIND, BF16>;
+    const TpSmem m = tp_smem(prm.k_pad, prm.rv, PSPLIT);
+    auto kfn = kmvm_tp_kernel<KIND, BF16, PSPLIT>;
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m.total);
     if (e != cudaSuccess) return e;
     kfn<<<plan.grid, kThreads, m.total, s>>>(a, b, v, prm);
@@ -442,9 +482,9 @@ cudaError_t launch_tp_typed(const TcPlan& plan, const TpParams& prm, const CUten
 
 }  // namespace
 
-bool tp_supported(int k_pad, int R_pad, int vsplit) {
+bool tp_supported(int k_pad, int R_pad, int vsplit, int psplit) {
     const int rv = R_pad * (1 + vsplit);
-    return k_pad <= 64 && rv <= 128 && rv % 32 == 0 && tp_smem(k_pad, rv).stages >= 2;
+    return k_pad <= 64 && rv <= 128 && rv % 32 == 0 && tp_smem(k_pad, rv, psplit).stages >= 2;
 }
 
 TcPlan tp_plan(const Ctx* ctx, int64_t Nr, int64_t Nc, int R, int k_pad, int vsplit) {
@@ -491,10 +531,11 @@ int launch_kmvm_tp(Ctx* ctx, const TcPlan& plan, const OperandLayout& L, const M
     prm.n_items = plan.n_it * plan.n_split;
     prm.k_pad = plan.k_pad;
     prm.rv = plan.rv;
-    const TpSmem m = tp_smem(plan.k_pad, plan.rv);
+    prm.psplit = L.psplit;
+    const TpSmem m = tp_smem(plan.k_pad, plan.rv, L.psplit);
     prm.stages = m.stages;
     prm.xi_bufs = m.xi_bufs;
-    if (!tp_supported(plan.k_pad, plan.R_pad, plan.rv / plan.R_pad - 1)) return GP_ERR_UNSUPPORTED;
+    if (!tp_supported(plan.k_pad, plan.R_pad, plan.rv / plan.R_pad - 1, L.psplit)) return GP_ERR_UNSUPPORTED;
     prm.diag = a.diag_coef != 0.0f ? 1 : 0;
     prm.ld_part = plan.Nr_pad;
     prm.partial = partial;
@@ -503,9 +544,14 @@ int launch_kmvm_tp(Ctx* ctx, const TcPlan& plan, const OperandLayout& L, const M
     const int bf = (L.prec == GP_PREC_BF16) ? 1 : 0;
     cudaError_t e = cudaErrorInvalidValue;
     prof_begin(ctx, s);
-#define GPK_TP_CASE(K)                                                                                  \
-    case K:                                                                                             \
-        e = bf ? launch_tp_typed<K, 1>(plan, prm, tmA, tmB, tmV, s) : launch_tp_typed<K, 0>(plan, prm, tmA, tmB, tmV, s); \
+#define GPK_TP_CASE(K)                                                                              \
+    case K:                                                                                         \
+        if (bf)                                                                                     \
+            e = L.psplit ? launch_tp_typed<K, 1, 1>(plan, prm, tmA, tmB, tmV, s)                     \
+                         : launch_tp_typed<K, 1, 0>(plan, prm, tmA, tmB, tmV, s);                    \
+        else                                                                                        \
+            e = L.psplit ? launch_tp_typed<K, 0, 1>(plan, prm, tmA, tmB, tmV, s)                     \
+                         : launch_tp_typed<K, 0, 0>(plan, prm, tmA, tmB, tmV, s);                    \
         break;
     switch (a.kernel) {
         GPK_TP_CASE(GP_KERNEL_RBF)

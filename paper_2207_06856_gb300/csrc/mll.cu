@@ -233,7 +233,7 @@ int mll_run(Ctx* ctx, WsCarver& wc, const gp_hyp_t* hyp, const float* X, const f
     // ---- gradient of the pseudo-loss (Eq. approx) ----
     if (pprobe) {
         WsCarver w2 = wc;
-        GPK_TRY(woodbury_apply(ctx, w2, pc->L, pc->core, rank, hyp->noise, N, B, R, nullptr, W, s));
+        GPK_TRY(woodbury_apply(ctx, w2, pc->L, pc->core, nullptr, rank, hyp->noise, N, B, R, nullptr, W, s));
     }
     pseudo_loss_operands_kernel<<<dim3(vg, R), 256, 0, s>>>(U, pprobe ? W : B, N, M, Uo, Wo);
     ctx->launches++;

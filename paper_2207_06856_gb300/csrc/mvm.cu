@@ -96,16 +96,21 @@ static int kop_plan(const Ctx* ctx, KOp& op, const gp_hyp_t* hyp, int64_t Nr, in
         if (xsplit && make_layout(hyp->d, op.prec, 1, 0, 0).k_pad == 0) xsplit = 0;   // does not fit
         const int single = (flags & GP_MVM_BF16_SINGLE) ? 1 : 0;
         int vsplit = bf ? !single : ((flags & GP_MVM_VSPLIT) ? 1 : 0);
-        const int psplit = bf ? !single : 0;
+        int psplit = bf ? !single : 0;
         const int Rc = R < 64 ? R : 64;
         const int Rp = ((Rc + 15) / 16) * 16;
         const OperandLayout probe = make_layout(hyp->d, op.prec, xsplit, 1, psplit);
-        // Pair engine (transposed value product) unless the kernel tile is split
-        // or the operands do not fit its shared-memory plan.  There FP16 always
-        // carries v as hi + lo: the lo rows share the MMA's M dimension.
-        const bool pair = !(flags & GP_MVM_ONE_TILE) && !psplit && probe.k_pad != 0 &&
-                          tp_supported(probe.k_pad, Rp, bf ? 0 : 1);
-        if (pair && !bf) vsplit = 1;
+        // Pair engine (transposed value product) unless asked otherwise or the
+        // operands do not fit its shared-memory plan.  There FP16 carries v as
+        // hi + lo (the lo rows share the MMA's M dimension) and, with
+        // GP_MVM_PSPLIT, the kernel tile as hi + lo too.
+        const int want_psplit = bf ? psplit : ((flags & GP_MVM_PSPLIT) ? 1 : 0);
+        const bool pair = !(flags & GP_MVM_ONE_TILE) && probe.k_pad != 0 &&
+                          tp_supported(probe.k_pad, Rp, bf ? vsplit : 1, want_psplit);
+        if (pair && !bf) {
+            vsplit = 1;
+            psplit = want_psplit;
+        }
         op.lay = make_layout(hyp->d, op.prec, xsplit, vsplit, psplit);
         if (op.lay.k_pad == 0) return GP_ERR_UNSUPPORTED;
         op.tp = pair ? tp_plan(ctx, Nr, Nc, Rc, op.lay.k_pad, vsplit) : tc_plan(ctx, Nr, Nc, Rc, op.lay.k_pad);

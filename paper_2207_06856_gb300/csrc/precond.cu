@@ -188,131 +188,161 @@ __global__ void core_chol_kernel(const double* __restrict__ partial, int nsplit,
 }
 
 // ---- Woodbury apply ---------------------------------------------------------------------
-constexpr int kWbRows = 256;
+// FP64 instructions are scarce on this GPU (a warp-wide FP64 FMA occupies its
+// pipe for tens of cycles), so the FP64 parts of the apply are spread over
+// many warps and never sit on a sequential path: C^{-1} is formed once per
+// solve, and every apply is  t = L^T w (FP32 within row blocks, FP64 across
+// them), u = C^{-1} t (one warp per output), z = (w - L u / sigma^2) / sigma^2.
 
-// tpart[blk][a][c] = sum_{i in blk rows} L[a][i] W[c][i]   (FP32 in-block, stored FP64)
+// Column j of C^{-1} = Lc^{-T} Lc^{-1} e_j: forward and backward substitution,
+// one warp per column, lane l holding rows l + 32 m (k <= 32 PER).
+// Lc is column-major: Lc(a, b) = core[b * k + a].
+template <int PER>
+__global__ void __launch_bounds__(256)
+core_inverse_kernel(const double* __restrict__ core, int k, double* __restrict__ cinv) {
+    const int j = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (j >= k) return;
+    double y[PER];
+#pragma unroll
+    for (int m = 0; m < PER; ++m) y[m] = (lane + 32 * m == j) ? 1.0 : 0.0;
+    // forward, column-oriented (entries above j stay zero)
+    for (int a = j; a < k; ++a) {
+        const double* col = core + (int64_t)a * k;
+        double ya = 0.0;
+#pragma unroll
+        for (int m = 0; m < PER; ++m)
+            if (lane + 32 * m == a) ya = y[m] / col[a];
+        ya = __shfl_sync(0xffffffffu, ya, a & 31);
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const int i = lane + 32 * m;
+            if (i == a) y[m] = ya;
+            else if (i > a && i < k) y[m] = fma(-col[i], ya, y[m]);
+        }
+    }
+    // backward, row-oriented: x_a = (y_a - sum_{i > a} Lc(i, a) x_i) / Lc(a, a)
+    for (int a = k - 1; a >= 0; --a) {
+        const double* col = core + (int64_t)a * k;
+        double sacc = 0.0;
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const int i = lane + 32 * m;
+            if (i > a && i < k) sacc = fma(col[i], y[m], sacc);
+        }
+        for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+#pragma unroll
+        for (int m = 0; m < PER; ++m)
+            if (lane + 32 * m == a) y[m] = (y[m] - sacc) / col[a];
+    }
+#pragma unroll
+    for (int m = 0; m < PER; ++m) {
+        const int a = lane + 32 * m;
+        if (a < k) cinv[(int64_t)j * k + a] = y[m];
+    }
+}
+
+// tpart[blk][a][c] = sum over this CTA's rows of L[a][i] W[c][i]: FP32
+// register blocks of 4 a x 4 c per thread over 32-row tiles staged in shared
+// memory (row-major, a or c fastest, float4 reads), stored as FP64.
+constexpr int kLtwTile = 32;
 __global__ void __launch_bounds__(256)
 wb_ltw_kernel(const float* __restrict__ L, int64_t N, int k, const float* __restrict__ W, int R,
-              const int* __restrict__ active, int64_t rows_per_blk, double* __restrict__ tpart) {
-    extern __shared__ float sh[];
-    constexpr int ST = kWbRows + 1;    // padded row stride: conflict-free column reads
-    float* sw = sh;                    // [R][ST]
-    float* sl = sh + R * ST;           // [16][ST]
+              int64_t rows_per_blk, int nab_pass, double* __restrict__ tpart) {
+    extern __shared__ float4 sh4[];
+    const int ncb = (R + 3) / 4;
+    const int lstride = nab_pass + 1;   // float4 units per staged row (one pad)
+    const int wstride = ncb + 1;
+    float4* sL = sh4;                              // [kLtwTile][lstride]
+    float4* sW = sh4 + kLtwTile * lstride;         // [kLtwTile][wstride]
+    float* sLf = reinterpret_cast<float*>(sL);
+    float* sWf = reinterpret_cast<float*>(sW);
     const int64_t r0 = rows_per_blk * blockIdx.x;
     const int64_t r1 = (r0 + rows_per_blk < N) ? r0 + rows_per_blk : N;
-    const int npair = 16 * R;
-    for (int a0 = 0; a0 < k; a0 += 16) {
-        // each thread owns up to 2 (a, c) pairs of this 16-column slab
-        float acc0 = 0.0f, acc1 = 0.0f;
-        for (int64_t i0 = r0; i0 < r1; i0 += kWbRows) {
+    const int ab = threadIdx.x % nab_pass, cb = threadIdx.x / nab_pass;
+    const bool worker = cb < ncb;
+    for (int a0 = 0; a0 < k; a0 += 4 * nab_pass) {
+        float acc[4][4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) acc[x][y] = 0.0f;
+        for (int64_t i0 = r0; i0 < r1; i0 += kLtwTile) {
             __syncthreads();
-            for (int e = threadIdx.x; e < R * kWbRows; e += blockDim.x) {
-                const int c = e / kWbRows, ii = e % kWbRows;
+            // stage L[a0 .. a0 + 4 nab_pass)[i0 .. i0 + 32) as [row][a] and W as [row][c]
+            for (int e = threadIdx.x; e < 4 * nab_pass * kLtwTile; e += blockDim.x) {
+                const int aa = e / kLtwTile, ii = e % kLtwTile;
                 const int64_t i = i0 + ii;
-                sw[c * ST + ii] = (i < r1) ? W[(int64_t)c * N + i] : 0.0f;
+                const int a = a0 + aa;
+                sLf[ii * 4 * lstride + aa] = (i < r1 && a < k) ? L[(int64_t)a * N + i] : 0.0f;
             }
-            for (int e = threadIdx.x; e < 16 * kWbRows; e += blockDim.x) {
-                const int aa = e / kWbRows, ii = e % kWbRows;
+            for (int e = threadIdx.x; e < 4 * ncb * kLtwTile; e += blockDim.x) {
+                const int cc = e / kLtwTile, ii = e % kLtwTile;
                 const int64_t i = i0 + ii;
-                sl[aa * ST + ii] = (i < r1 && a0 + aa < k) ? L[(int64_t)(a0 + aa) * N + i] : 0.0f;
+                sWf[ii * 4 * wstride + cc] = (i < r1 && cc < R) ? W[(int64_t)cc * N + i] : 0.0f;
             }
             __syncthreads();
-            for (int q = 0; q < 2; ++q) {
-                const int pr = threadIdx.x + q * blockDim.x;
-                if (pr < npair) {
-                    const int aa = pr % 16, c = pr / 16;
-                    const float* wl = sw + c * ST;
-                    const float* ll = sl + aa * ST;
-                    float acc = 0.0f;
-                    for (int ii = 0; ii < kWbRows; ++ii) acc = fmaf(ll[ii], wl[ii], acc);
-                    if (q == 0) acc0 += acc; else acc1 += acc;
+            if (worker) {
+#pragma unroll 8
+                for (int ii = 0; ii < kLtwTile; ++ii) {
+                    const float4 l4 = sL[ii * lstride + ab];
+                    const float4 w4 = sW[ii * wstride + cb];
+                    const float lv[4] = {l4.x, l4.y, l4.z, l4.w};
+                    const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                    for (int x = 0; x < 4; ++x)
+#pragma unroll
+                        for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(lv[x], wv[y], acc[x][y]);
                 }
             }
         }
-        for (int q = 0; q < 2; ++q) {
-            const int pr = threadIdx.x + q * blockDim.x;
-            if (pr < npair) {
-                const int aa = pr % 16, c = pr / 16;
-                if (a0 + aa < k)
-                    tpart[((int64_t)blockIdx.x * k + a0 + aa) * R + c] = (double)(q == 0 ? acc0 : acc1);
+        if (worker) {
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                const int a = a0 + 4 * ab + x;
+#pragma unroll
+                for (int y = 0; y < 4; ++y) {
+                    const int c = 4 * cb + y;
+                    if (a < k && c < R) tpart[((int64_t)blockIdx.x * k + a) * R + c] = (double)acc[x][y];
+                }
             }
         }
     }
 }
 
-// One warp per right-hand side: t = sum of partials (fixed order),
-// u = C^{-1} t with C = Lc Lc^T (forward then backward substitution, FP64).
-// grid = ceil(R / 8) CTAs of 8 warps; CTA b solves columns 8b .. 8b+7.
-constexpr int kWbSolveWarps = 8;
-__global__ void __launch_bounds__(kWbSolveWarps * 32)
-wb_solve_kernel(const double* __restrict__ tpart, int nblk, int k, int R, const double* __restrict__ core,
-                float* __restrict__ u_out, double* __restrict__ ybuf) {
-    const int c0 = blockIdx.x * kWbSolveWarps;
-    const int nc = (R - c0) < kWbSolveWarps ? (R - c0) : kWbSolveWarps;
-    // t = sum over row blocks (fixed order) for this CTA's columns, layout [a][c]
-    for (int e = threadIdx.x; e < k * nc; e += blockDim.x) {
-        const int a = e / nc, c = c0 + e % nc;
-        double t = 0.0;
-        for (int b = 0; b < nblk; ++b) t += tpart[((int64_t)b * k + a) * R + c];
-        ybuf[a * R + c] = t;
-    }
-    __syncthreads();
-    // One warp per right-hand side; lane l keeps rows a = l + 32 m in registers
-    // (k <= 512).  core holds Lc column-major: Lc(a, b) = core[b * k + a].
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int kMaxPer = 16;
-    if (w < nc) {
-        const int c = c0 + w;
-        double y[kMaxPer];
-#pragma unroll
-        for (int m = 0; m < kMaxPer; ++m) {
-            const int a = lane + 32 * m;
-            y[m] = a < k ? ybuf[a * R + c] : 0.0;
-        }
-        // forward, column-oriented: y_a /= Lc(a,a); y_i -= Lc(i,a) y_a for i > a
-        for (int a = 0; a < k; ++a) {
-            const double* col = core + (int64_t)a * k;
-            double ya = 0.0;
-#pragma unroll
-            for (int m = 0; m < kMaxPer; ++m)
-                if (lane + 32 * m == a) ya = y[m] / col[a];
-            ya = __shfl_sync(0xffffffffu, ya, a & 31);
-#pragma unroll
-            for (int m = 0; m < kMaxPer; ++m) {
-                const int i = lane + 32 * m;
-                if (i == a) y[m] = ya;
-                else if (i > a && i < k) y[m] = fma(-col[i], ya, y[m]);
-            }
-        }
-        // backward, row-oriented: u_a = (y_a - sum_{j > a} Lc(j,a) u_j) / Lc(a,a)
-        for (int a = k - 1; a >= 0; --a) {
-            const double* col = core + (int64_t)a * k;
-            double sacc = 0.0;
-#pragma unroll
-            for (int m = 0; m < kMaxPer; ++m) {
-                const int j = lane + 32 * m;
-                if (j > a && j < k) sacc = fma(col[j], y[m], sacc);
-            }
-            for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-#pragma unroll
-            for (int m = 0; m < kMaxPer; ++m)
-                if (lane + 32 * m == a) y[m] = (y[m] - sacc) / col[a];
-        }
-#pragma unroll
-        for (int m = 0; m < kMaxPer; ++m) {
-            const int a = lane + 32 * m;
-            if (a < k) u_out[a * R + c] = (float)y[m];
-        }
-    }
+// t[a][c] = sum over blocks of tpart (fixed order within each lane, fixed
+// shuffle tree across lanes); one warp per (a, c).
+__global__ void __launch_bounds__(256)
+wb_reduce_kernel(const double* __restrict__ tpart, int nblk, int k, int R, double* __restrict__ t) {
+    const int e = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (e >= k * R) return;
+    double v = 0.0;
+    for (int b = lane; b < nblk; b += 32) v += tpart[(int64_t)b * k * R + e];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) t[e] = v;
+}
+
+// u[a][c] = sum_b C^{-1}[a][b] t[b][c] (FP64), stored FP32; one warp per (a, c).
+__global__ void __launch_bounds__(256)
+wb_gemv_kernel(const double* __restrict__ cinv, const double* __restrict__ t, int k, int R, float* __restrict__ u) {
+    const int e = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (e >= k * R) return;
+    const int a = e / R, c = e % R;
+    double v = 0.0;
+    for (int b = lane; b < k; b += 32) v = fma(cinv[(int64_t)a * k + b], t[b * R + c], v);   // C^{-1} symmetric
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) u[e] = (float)v;
 }
 
 // z[c][i] = inv_s2 w[c][i] - inv_s4 sum_a L[a][i] u[a][c]   (active columns only)
+// u staged in shared memory as [a][RB] (RB a multiple of 4: float4 reads,
+// the same address across the warp).
 template <int RB>
 __global__ void __launch_bounds__(256)
 wb_out_kernel(const float* __restrict__ L, int64_t N, int k, const float* __restrict__ W, int R, int c0,
               const float* __restrict__ u, float inv_s2, float inv_s4, const int* __restrict__ active,
               float* __restrict__ Z) {
-    extern __shared__ float su[];   // [k][RB]
+    extern __shared__ float4 su4[];   // [k][RB / 4]
+    float* su = reinterpret_cast<float*>(su4);
     const int rc = (R - c0) < RB ? (R - c0) : RB;
     for (int e = threadIdx.x; e < k * RB; e += blockDim.x) {
         const int a = e / RB, cc = e % RB;
@@ -326,7 +356,13 @@ wb_out_kernel(const float* __restrict__ L, int64_t N, int k, const float* __rest
         for (int a = 0; a < k; ++a) {
             const float la = L[(int64_t)a * N + i];
 #pragma unroll
-            for (int cc = 0; cc < RB; ++cc) acc[cc] = fmaf(la, su[a * RB + cc], acc[cc]);
+            for (int q = 0; q < RB / 4; ++q) {
+                const float4 u4 = su4[a * (RB / 4) + q];
+                acc[4 * q] = fmaf(la, u4.x, acc[4 * q]);
+                acc[4 * q + 1] = fmaf(la, u4.y, acc[4 * q + 1]);
+                acc[4 * q + 2] = fmaf(la, u4.z, acc[4 * q + 2]);
+                acc[4 * q + 3] = fmaf(la, u4.w, acc[4 * q + 3]);
+            }
         }
 #pragma unroll
         for (int cc = 0; cc < RB; ++cc) {
@@ -431,47 +467,78 @@ int pivchol_run(Ctx* ctx, WsCarver& wc, const gp_hyp_t* hyp, const float* X, int
 }
 
 // ---- Woodbury apply ----
+namespace {
+int ltw_grid(const Ctx* ctx, int64_t N, int64_t* rows_per) {
+    const int64_t G = 2 * (int64_t)(ctx->num_sms > 0 ? ctx->num_sms : 148);
+    int64_t rp = (N + G - 1) / G;
+    rp = ((rp + kLtwTile - 1) / kLtwTile) * kLtwTile;
+    if (rp < kLtwTile) rp = kLtwTile;
+    *rows_per = rp;
+    return (int)((N + rp - 1) / rp);
+}
+}  // namespace
+
 size_t woodbury_workspace(const Ctx* ctx, int64_t N, int k, int R) {
-    (void)ctx;
     WsCounter c;
-    const int64_t rows_per = N < 65536 ? kWbRows : ((N / 256 + kWbRows - 1) / kWbRows) * kWbRows;
-    const int64_t nblk = (N + rows_per - 1) / rows_per;
-    c.take<double>((size_t)nblk * k * R);
-    c.take<double>((size_t)k * R);
-    c.take<float>((size_t)k * R);
+    int64_t rp = 0;
+    const int nblk = ltw_grid(ctx, N, &rp);
+    c.take<double>((size_t)nblk * k * R);   // partials
+    c.take<double>((size_t)k * R);          // t
+    c.take<float>((size_t)k * R);           // u
+    c.take<double>((size_t)k * k);          // C^{-1} when the caller has none
     return c.off;
 }
 
-int woodbury_apply(Ctx* ctx, WsCarver& wc, const float* L, const double* core, int k, double noise, int64_t N,
-                   const float* W, int R, const int* active, float* Z, cudaStream_t s) {
-    const int64_t rows_per = N < 65536 ? kWbRows : ((N / 256 + kWbRows - 1) / kWbRows) * kWbRows;
-    const int64_t nblk = (N + rows_per - 1) / rows_per;
+int woodbury_prepare(Ctx* ctx, const double* core, int k, double* cinv, cudaStream_t s) {
+    const unsigned g = (unsigned)((k + 7) / 8);
+    if (k <= 128) core_inverse_kernel<4><<<g, 256, 0, s>>>(core, k, cinv);
+    else if (k <= 256) core_inverse_kernel<8><<<g, 256, 0, s>>>(core, k, cinv);
+    else core_inverse_kernel<16><<<g, 256, 0, s>>>(core, k, cinv);
+    ctx->launches++;
+    return cudaGetLastError() == cudaSuccess ? GP_OK : GP_ERR_CUDA;
+}
+
+int woodbury_apply(Ctx* ctx, WsCarver& wc, const float* L, const double* core, const double* cinv, int k,
+                   double noise, int64_t N, const float* W, int R, const int* active, float* Z, cudaStream_t s) {
+    int64_t rows_per = 0;
+    const int nblk = ltw_grid(ctx, N, &rows_per);
     double* tpart = wc.take<double>((size_t)nblk * k * R);
-    double* ybuf = wc.take<double>((size_t)k * R);
+    double* t = wc.take<double>((size_t)k * R);
     float* u = wc.take<float>((size_t)k * R);
+    double* cinv_own = wc.take<double>((size_t)k * k);
     if (!wc.ok) return GP_ERR_WORKSPACE;
-    const size_t sh1 = (size_t)(R + 16) * (kWbRows + 1) * sizeof(float);
-    if (sh1 > 48 * 1024) {
-        if (cudaFuncSetAttribute(wb_ltw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh1) != cudaSuccess)
-            return GP_ERR_CUDA;
+    if (R > 64 || k > 512) return GP_ERR_UNSUPPORTED;
+    if (!cinv) {
+        GPK_TRY(woodbury_prepare(ctx, core, k, cinv_own, s));
+        cinv = cinv_own;
     }
-    if (16 * R > 512) return GP_ERR_UNSUPPORTED;
-    wb_ltw_kernel<<<(unsigned)nblk, 256, sh1, s>>>(L, N, k, W, R, active, rows_per, tpart);
+    const int ncb = (R + 3) / 4;
+    const int nab_all = (k + 3) / 4;
+    int nab_pass = 256 / ncb;
+    if (nab_pass > nab_all) nab_pass = nab_all;
+    const size_t sh1 = (size_t)kLtwTile * ((nab_pass + 1) + (ncb + 1)) * sizeof(float4);
+    if (sh1 > 48 * 1024 &&
+        cudaFuncSetAttribute(wb_ltw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh1) != cudaSuccess)
+        return GP_ERR_CUDA;
+    wb_ltw_kernel<<<(unsigned)nblk, 256, sh1, s>>>(L, N, k, W, R, rows_per, nab_pass, tpart);
     ctx->launches++;
-    wb_solve_kernel<<<(unsigned)((R + kWbSolveWarps - 1) / kWbSolveWarps), kWbSolveWarps * 32, 0, s>>>(
-        tpart, (int)nblk, k, R, core, u, ybuf);
-    ctx->launches++;
+    const unsigned gw = (unsigned)((k * R + 7) / 8);
+    wb_reduce_kernel<<<gw, 256, 0, s>>>(tpart, nblk, k, R, t);
+    wb_gemv_kernel<<<gw, 256, 0, s>>>(cinv, t, k, R, u);
+    ctx->launches += 2;
     const float inv_s2 = (float)(1.0 / noise), inv_s4 = (float)(1.0 / (noise * noise));
     int64_t g = (N + 255) / 256;
     const int64_t cap = 4 * (int64_t)(ctx->num_sms > 0 ? ctx->num_sms : 148);
     if (g > cap) g = cap;
-    const int RB = R <= 8 ? 8 : (R <= 16 ? 16 : 32);
+    const int RB = R <= 8 ? 8 : (R <= 16 ? 16 : (R <= 24 ? 24 : 32));
     for (int c0 = 0; c0 < R; c0 += RB) {
         const size_t sh = (size_t)k * RB * sizeof(float);
         if (RB == 8)
             wb_out_kernel<8><<<(unsigned)g, 256, sh, s>>>(L, N, k, W, R, c0, u, inv_s2, inv_s4, active, Z);
         else if (RB == 16)
             wb_out_kernel<16><<<(unsigned)g, 256, sh, s>>>(L, N, k, W, R, c0, u, inv_s2, inv_s4, active, Z);
+        else if (RB == 24)
+            wb_out_kernel<24><<<(unsigned)g, 256, sh, s>>>(L, N, k, W, R, c0, u, inv_s2, inv_s4, active, Z);
         else
             wb_out_kernel<32><<<(unsigned)g, 256, sh, s>>>(L, N, k, W, R, c0, u, inv_s2, inv_s4, active, Z);
         ctx->launches++;

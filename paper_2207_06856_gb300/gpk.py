@@ -45,6 +45,7 @@ MVM_SCALE_SQRT_N = 0x800
 MVM_VSPLIT = 0x1000
 MVM_BF16_SINGLE = 0x2000
 MVM_ONE_TILE = 0x4000
+MVM_PSPLIT = 0x8000
 
 
 class GPKError(RuntimeError):
@@ -600,3 +601,4 @@ class Server:
             self.close()
         except Exception:
             pass
+

@@ -75,15 +75,16 @@ def test_kmvm_matches_oracle(ctx, prec, kern, shape):
 @pytest.mark.parametrize("shape", [(129, 4, 16), (700, 8, 17), (333, 18, 17), (257, 16, 33), (2048, 8, 64)])
 def test_kmvm_engines_agree_with_oracle(ctx, prec, kern, shape):
     """Both tensor-core engines (row-tile pairs with the transposed value
-    product, the default; one row tile with P V) meet the tolerance, FP16 and
-    single-term BF16 (which both engines run)."""
+    product, the default; one row tile with P V) meet the tolerance, FP16 (the
+    pair engine with single-term P, the default, and with the tile as hi + lo)
+    and single-term BF16 (which both engines run)."""
     from paper_2207_06856_gb300 import gpk
     N, d, R = shape
     X, V, _, ls, a2, s2 = workloads.random_problem(N, d, R, seed=3 * N + d, kernel=kern)
     ref = _ref(X, V, kern, ls, a2, s2)
     base = gpk.MVM_BF16_SINGLE if prec == "bf16" else 0
     tol = 8e-3 if prec == "bf16" else TOL[prec]
-    for fl in (0, gpk.MVM_ONE_TILE):
+    for fl in (0, gpk.MVM_ONE_TILE, gpk.MVM_PSPLIT):
         got = _run(ctx, X, V, kern, ls, a2, s2, prec, flags=base | fl)
         assert _colerr(got, ref) <= tol, (fl, _colerr(got, ref))
 
@@ -213,3 +214,4 @@ def test_kmvm_rejects_bad_arguments(ctx):
                  add_noise=True)
     with pytest.raises(gpk.GPKError):
         gpk.kmvm(ctx, gpk.Hyper(0, np.ones(3), 1.0, 0.1), X, torch.randn(65, 10, device=dev))
+
