@@ -41,6 +41,9 @@ UNIT = "s"
 TOL = 1e-2
 MAX_ITER = 1000
 FP32_ITERS_NOTE = "iterations of the FP32 stable CG on this workload"
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one kmvm_tp_kernel launch on the
+# precision workload (N = 65,536, R = 17, FP16); must be re-measured when the kernel changes
+KMVM_TRAFFIC_BYTES = 12.662272e6 + 12.241408e6
 
 
 def _peaks_file():
@@ -98,6 +101,18 @@ class ClockSampler:
                           and "Not" not in r[4 + i]})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": reasons, "samples": len(self.rows)}
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """The largest x over all ranks of the initialised process group (x itself
+    when there is none).  Replicas are timed by their slowest member."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def _rank_env():
@@ -217,11 +232,7 @@ def run_ours(args):
     gpu_launches = ctx.launches - launches0
     # launches inside the timed steps only (warm-up solves launch the same number)
     gpu_launches = int(round(gpu_launches * args.steps / (args.steps + args.warmup)))
-    t_step = float(np.mean(times))
-    if world > 1:
-        t = torch.tensor([t_step], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_step = float(t.item())
+    t_step = max_over_ranks(float(np.mean(times)), dev)
 
     # --- residual recomputed in FP64 on sampled rows (verification, untimed) -------------
     resid = None
@@ -239,11 +250,19 @@ def run_ours(args):
     mufu_per_pair = 1 if w.kernel == gpk.RBF else 2
     peak_meas = peaks["ex2_per_s"] / mufu_per_pair / 1e9 if w.kernel == gpk.RBF else \
         1.0 / (1.0 / peaks["ex2_per_s"] + 1.0 / peaks["sqrt_per_s"]) / 1e9
+    # FP16 RBF: each pair also needs half an FP32 -> FP16x2 conversion on the same unit
+    mix_peak = peaks.get("fp16_epilogue_values_per_s", float("nan")) / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_meas, "unit": "Gpairs/s",
-                "frac": achieved / peak_meas, "traffic": None,
-                "kernel": "kmvm_tc_kernel (FP16 tensor-core kernel MVM)",
+                "frac": achieved / peak_meas,
+                # DRAM bytes per launch from the ncu capture of this kernel on this workload
+                # (profiles/kmvm_tp_fp16_precision.md): 12.66 MB read + 12.24 MB written
+                "traffic": KMVM_TRAFFIC_BYTES if (w.kernel == gpk.RBF and args.precision == "fp16") else None,
+                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+                "kernel": "kmvm_tp_kernel (tcgen05 S = X_i X_j^T and transposed value product "
+                          "O^T = Vt_j P^T over row-tile pairs; kernel function on the SFU)",
                 "peak_source": "measured special-function-unit ex2 rate on this GPU (gp_measure_peaks), "
                                f"{mufu_per_pair} SFU op(s) per kernel pair",
+                "frac_of_sfu_ex2_plus_fp16_pack": (achieved / mix_peak) if (w.kernel == gpk.RBF and mix_peak > 0) else None,
                 "units_per_launch": pairs_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
                 "launches_timed": prof_n, "measured_unit_peaks": peaks}
 
@@ -252,6 +271,8 @@ def run_ours(args):
     if not args.no_arms:
         for name, prec, alg, ro in [("fp32_plain_alg1", "fp32", "standard", "none"),
                                     ("bf16_stable_alg2", "bf16", "stable", "pinv"),
+                                    ("fp16_split_tile_and_inputs_stable_alg2",
+                                     gpk.FP16 | gpk.MVM_PSPLIT | gpk.MVM_XSPLIT, "stable", "pinv"),
                                     ("fp32_stable_alg2", "fp32", "stable", "pinv")]:
             ts, inf, _ = timed(prec, alg, ro, max(1, min(args.steps, 2)), 1)
             arms[name] = {"s_per_solve": float(np.mean(ts)), "iters": int(inf[-1]["iters"]),
