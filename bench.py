@@ -397,7 +397,8 @@ def run_serve(args):
     inputs = [(gpk.Hyper(r.kernel, r.lengthscale, r.outputscale, r.noise), pin(r.X), pin(r.y), pin(r.Xstar))
               for r in reqs]
     srv = gpk.Server(0, arena_bytes=int(args.serve_arena_gb * (1 << 30)), max_slots=args.serve_slots, rank=20,
-                     precision="fp16", mean_precision="fp32", tol=TOL, max_iter=1000, restarts=4)
+                     precision=gpk.FP16 | gpk.MVM_PSPLIT | gpk.MVM_XSPLIT, mean_precision="fp32", tol=TOL,
+                     max_iter=1000, restarts=4)
     small = workloads.serving(n_requests=3, rate_per_s=1.0, seed=2, n_min=1000, n_max=2000)
     for r in small:   # warm-up
         srv.submit(gpk.Hyper(r.kernel, r.lengthscale, r.outputscale, r.noise), r.X, r.y, r.Xstar).result()
@@ -444,7 +445,8 @@ def run_serve(args):
         "vs_baseline": None, "dtype": "fp16", "data": "synthetic",
         "config": {"workload": f"serving: {len(reqs)} posterior-mean requests, Poisson arrivals at "
                                f"{args.serve_load:.2f}x saturated rate, N log-uniform [1k, 200k], d in {{4,8,16}}, "
-                               "RBF/Matern-3/2, 1024 test points, FP16 MVM + stable CG to 1e-2, rank 20",
+                               "RBF/Matern-3/2, 1024 test points, FP16 tensor-core MVM (kernel tile and inputs "
+                               "as hi + lo) + stable CG to 1e-2, rank 20",
                    "slots": args.serve_slots, "arena_gb": args.serve_arena_gb},
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
         "mean_ms": float(lat.mean()), "solves_per_s": len(reqs) / wall, "saturated_solves_per_s": sat,

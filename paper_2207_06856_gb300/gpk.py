@@ -545,11 +545,15 @@ class Server:
 
     Each request solves (K + sigma^2 I) v = y with the stable preconditioned CG
     and returns mu* = K(X*, X) v.  Inputs are copied into page-locked host
-    tensors at submit so the library's uploads are asynchronous."""
+    tensors at submit so the library's uploads are asynchronous.  The default
+    CG precision is FP16 tensor-core operands with the kernel tile and the
+    inputs carried as hi + lo: over the serving workload's range of noise
+    levels it needs the FP32 iteration count, where a single FP16 rounding of
+    the kernel tile can leave the operator too inexact for CG to converge."""
 
     def __init__(self, device: int = 0, arena_bytes: int = 8 << 30, max_slots: int = 8, rank: int = 20,
-                 precision="fp16", mean_precision="fp32", tol: float = 1e-2, max_iter: int = 1000,
-                 restarts: int = 4, reorth="pinv"):
+                 precision=FP16 | MVM_PSPLIT | MVM_XSPLIT, mean_precision="fp32", tol: float = 1e-2,
+                 max_iter: int = 1000, restarts: int = 4, reorth="pinv"):
         self.opts = _server_opts(arena_bytes, max_slots, rank, precision, mean_precision, tol, max_iter, restarts,
                                  reorth)
         h = _c_void_p()

@@ -58,7 +58,8 @@ def test_serve_fp32_matches_exact_posterior_mean(gpk):
 
 @pytest.mark.gpu
 def test_serve_fp16_within_cg_bound(gpk):
-    """The served configuration (FP16 tensor-core MVM, CG to 1e-2, rank 20):
+    """The served configuration (FP16 tensor-core MVM with hi + lo tile and
+    inputs, CG to 1e-2, rank 20):
     the reported residual is <= 1e-2 and the mean is within the bound that
     residual implies: mu - mu_exact = K* Ktilde^{-1} r, so
     ||mu - mu_exact|| <= ||K* Ktilde^{-1}||_2 ||r||, ||r|| = rel_resid ||y||
