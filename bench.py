@@ -459,6 +459,118 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_diff(args):
+    """Differentiation workload: N = 262,144, d = 18 (ARD RBF, Gaussian-mixture
+    inputs, random-feature targets), the training loop of the paper: Adam on the
+    hyperparameters, each step one MLL + gradient (CG to 1.0 with 10 iterations
+    at least and 50 at most, 16 P-distributed probes, SLQ log-determinant,
+    rank-100 preconditioner, FP16 tensor-core MVM, hand-written backward)."""
+    import torch
+    from paper_2207_06856_gb300 import autograd, gpk, workloads
+    torch.cuda.set_device(0)
+    w = workloads.differentiation(N=args.diff_n)
+    ctx = gpk.Context(0)
+    X = torch.from_numpy(w.X).cuda()
+    y = torch.from_numpy(w.y).cuda()
+    step_s = []
+    t_last = [None]
+
+    def cb(step, rec):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        step_s.append(t - t_last[0])
+        t_last[0] = t
+
+    launches0 = ctx.launches
+    sampler = ClockSampler(0)
+    sampler.start()
+    torch.cuda.synchronize()
+    t_last[0] = time.perf_counter()
+    hist = autograd.fit(ctx, X, y, w.kernel, w.lengthscale, w.outputscale, w.noise, steps=args.diff_steps, lr=0.05,
+                        M=16, rank=w.rank, tol=args.diff_tol, max_iter=args.diff_max_iter, min_iter=10,
+                        precision=args.precision, callback=cb)
+    clocks = sampler.stop()
+    timed = step_s[1:] if len(step_s) > 1 else step_s   # the first step also builds the workspace
+    iters = [int(h[4]["iters"]) for h in hist]
+    # progress check with the FP64 oracle: exact negative log marginal likelihood of a
+    # random 3,000-point subsample at the initial and the final hyperparameters
+    import oracle as O
+    sub = np.sort(np.random.default_rng(11).choice(w.X.shape[0], 3000, replace=False))
+    Xs, ys = w.X[sub], w.y[sub]
+    kn = workloads.KERNEL_NAMES[w.kernel]
+    nll0 = O.mll_exact(Xs, ys, O.Hyp(kn, w.lengthscale.astype(np.float64), w.outputscale, w.noise))
+    nll1 = O.mll_exact(Xs, ys, O.Hyp(kn, np.asarray(hist[-1][1], np.float64), hist[-1][2], hist[-1][3]))
+    line = {
+        "metric": "adam_step_time", "value": float(np.mean(timed)), "unit": "s", "n_gpus": 1,
+        "steps": len(timed), "warmup": len(step_s) - len(timed), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": f"differentiation: N={w.X.shape[0]} d=18 ARD RBF, 8-component Gaussian mixture, "
+                               "random-feature GP targets + noise 0.1, 16 P-distributed probes, SLQ log-det, rank 100, "
+                               f"CG tol {args.diff_tol} (10..{args.diff_max_iter} iterations), Adam lr 0.05 on "
+                               "softplus parameters"},
+        "loss_first": hist[0][0], "loss_last": hist[-1][0],
+        "subsample_exact_nll_initial": nll0, "subsample_exact_nll_final": nll1,
+        "lengthscale_last": [float(v) for v in hist[-1][1]], "outputscale_last": hist[-1][2],
+        "noise_last": hist[-1][3], "cg_iters": iters, "total_s": float(np.sum(step_s)),
+        "gpu_launches": int(ctx.launches - launches0), "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_scale(args):
+    """Scale workload: N = 1,843,200, d = 11, Matern-3/2 ARD: one full MLL +
+    gradient step (rank-100 pivoted Cholesky, 1 + 16 right-hand sides with
+    P-distributed probes, CG to 1.0 with 10..50 iterations, SLQ log-det, FP16
+    tensor-core MVM, hand-written backward).  Checks the solves on sampled rows
+    with the FP64 oracle."""
+    import torch
+    from paper_2207_06856_gb300 import gpk, workloads
+    torch.cuda.set_device(0)
+    w = workloads.scale(N=args.scale_n)
+    N, d = w.X.shape
+    hyp = gpk.Hyper(w.kernel, w.lengthscale, w.outputscale, w.noise)
+    ctx = gpk.Context(0)
+    X = torch.from_numpy(w.X).cuda()
+    y = torch.from_numpy(w.y).cuda()
+    rng = np.random.default_rng(7)
+    Z = torch.from_numpy(rng.standard_normal((16, N)).astype(np.float32)).cuda()
+    E = torch.from_numpy(rng.standard_normal((16, w.rank)).astype(np.float32)).cuda()
+    sampler = ClockSampler(0)
+    launches0 = ctx.launches
+    sampler.start()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    pc = gpk.pivchol(ctx, hyp, X, w.rank)
+    mll, g, _, U, info = gpk.mll_and_grad(ctx, hyp, X, y, Z, precond=pc, E=E, precond_probes=True, want_logdet=True,
+                                          tol=w.tol, min_iter=10, max_iter=w.max_iter, precision=args.precision,
+                                          return_U=True)
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    t = e0.elapsed_time(e1) / 1e3
+    # sampled FP64 check of the y-solve: residual of column 0 on 512 rows
+    import oracle as O
+    rows = np.sort(np.random.default_rng(3).choice(N, 512, replace=False))
+    oh = O.Hyp(workloads.KERNEL_NAMES[w.kernel], w.lengthscale, w.outputscale, w.noise)
+    u0 = U[0].cpu().numpy().astype(np.float64)
+    r = O.kmvm_rows(w.X, rows, u0[:, None], oh)[:, 0] - w.y[rows].astype(np.float64)
+    est = float(np.sqrt(N / len(rows) * np.sum(r * r)) / np.linalg.norm(w.y.astype(np.float64)))
+    line = {
+        "metric": "mll_gradient_step_time", "value": t, "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+        "data": "synthetic",
+        "config": {"workload": f"scale: N={N} d=11 Matern-3/2 ARD, 16-component anisotropic Gaussian mixture, "
+                               "rank-100 pivoted Cholesky, 1+16 RHS (P-distributed probes), CG tol 1.0 "
+                               "(10..50 iterations), SLQ log-det"},
+        "mll": mll, "grad": [float(v) for v in g], "cg_iters": int(info["iters"]),
+        "rel_resid_y_reported": float(info["rel_resid"][0]), "rel_resid_y_fp64_sampled_512_rows": est,
+        "pairs_per_mvm": float(N) * float(N), "gpu_launches": int(ctx.launches - launches0), "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -472,7 +584,12 @@ def main():
     ap.add_argument("--skip-verify", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-iters", type=int, default=152)
-    ap.add_argument("--mode", default="solve", choices=["solve", "kmvm", "serve"])
+    ap.add_argument("--mode", default="solve", choices=["solve", "kmvm", "serve", "diff", "scale"])
+    ap.add_argument("--diff-steps", type=int, default=20)
+    ap.add_argument("--diff-n", type=int, default=262144)
+    ap.add_argument("--diff-tol", type=float, default=1.0)
+    ap.add_argument("--diff-max-iter", type=int, default=50)
+    ap.add_argument("--scale-n", type=int, default=1843200)
     ap.add_argument("--one-tile", action="store_true", help="kmvm mode: the one-row-tile tensor-core engine")
     ap.add_argument("--psplit", action="store_true", help="kmvm mode: FP16 kernel tile as hi + lo")
     ap.add_argument("--serve-requests", type=int, default=512)
@@ -485,6 +602,10 @@ def main():
         run_kmvm(args)
     elif args.mode == "serve":
         run_serve(args)
+    elif args.mode == "diff":
+        run_diff(args)
+    elif args.mode == "scale":
+        run_scale(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

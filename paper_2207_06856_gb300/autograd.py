@@ -34,7 +34,7 @@ class MarginalLikelihood(torch.autograd.Function):
         mll, g, gX, _, info = gpk.mll_and_grad(
             cfg.ctx, hyp, X, y, Z, precond=pc, E=E if cfg.precond_probes else None,
             precond_probes=cfg.precond_probes, want_logdet=cfg.want_logdet, tol=cfg.tol, max_iter=cfg.max_iter,
-            precision=cfg.precision, want_X=X.requires_grad)
+            min_iter=cfg.min_iter, precision=cfg.precision, want_X=X.requires_grad)
         cfg.last_info = info
         d = hyp.d
         fctx.grads = (torch.tensor(g[:d], dtype=lengthscale.dtype, device=lengthscale.device),
@@ -56,7 +56,8 @@ class FitConfig:
     rank: int = 100
     tol: float = 1.0
     max_iter: int = 50
-    precision: str = "fp16"
+    min_iter: int = 10
+    precision: object = "fp16"
     precond_probes: bool = True
     want_logdet: bool = True
     last_info: dict | None = None
@@ -68,11 +69,12 @@ def softplus_inv(x: float) -> float:
 
 def fit(ctx, X, y, kernel: int, init_lengthscale, init_outputscale: float, init_noise: float, steps: int = 20,
         lr: float = 0.05, M: int = 16, rank: int = 100, tol: float = 1.0, max_iter: int = 50,
-        precision: str = "fp16", seed: int = 0, min_noise: float = 1e-4, callback=None):
+        precision="fp16", seed: int = 0, min_noise: float = 1e-4, callback=None, min_iter: int = 10):
     """Adam on softplus-raw (l, a^2, sigma^2) for `steps` steps (the paper's
-    training loop: Adam, CG tolerance 1.0 by default).  Probes are redrawn
-    every step from a seeded generator (standard normals z~ and e, used as
-    z = L e + sigma z~).  Returns the history [(loss, l, a^2, sigma^2)]."""
+    training loop: Adam, CG tolerance 1.0 with an iteration floor by default).
+    Probes are redrawn every step from a seeded generator (standard normals z~
+    and e, used as z = L e + sigma z~).  Returns the history
+    [(loss, l, a^2, sigma^2, info)]."""
     dev = X.device
     d = X.shape[1]
     raw_l = torch.tensor([softplus_inv(float(v)) for v in np.atleast_1d(init_lengthscale)], dtype=torch.float64,
@@ -80,7 +82,8 @@ def fit(ctx, X, y, kernel: int, init_lengthscale, init_outputscale: float, init_
     raw_a = torch.tensor(softplus_inv(init_outputscale), dtype=torch.float64, requires_grad=True)
     raw_s = torch.tensor(softplus_inv(max(init_noise - min_noise, 1e-6)), dtype=torch.float64, requires_grad=True)
     opt = torch.optim.Adam([raw_l, raw_a, raw_s], lr=lr)
-    cfg = FitConfig(ctx=ctx, kernel=kernel, rank=rank, tol=tol, max_iter=max_iter, precision=precision)
+    cfg = FitConfig(ctx=ctx, kernel=kernel, rank=rank, tol=tol, max_iter=max_iter, min_iter=min_iter,
+                    precision=precision)
     gen = torch.Generator(device="cpu").manual_seed(seed)
     hist = []
     for step in range(steps):

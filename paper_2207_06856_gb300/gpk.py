@@ -462,15 +462,17 @@ def slq_quadrature(alpha, beta, gamma0: float) -> float:
 def mll_and_grad(ctx: Context, hyp: Hyper, X, y, Z, precond: Precond | None = None, E=None,
                  precond_probes: bool = False, want_logdet: bool = True, tol: float = 1e-2, max_iter: int = 100,
                  precision="fp16", want_X: bool = False, return_U: bool = False, restarts: int = 4,
-                 check_precision="fp32", escalate: bool = True, stream=None):
+                 check_precision="fp32", escalate: bool = True, min_iter: int = 0, stream=None):
     """gp_mll_and_grad.  X (N, d), y (N,), Z (M, N) probes [, E (M, rank) normals]
-    -> (mll, grad (numpy, d + 2), grad_X or None, U or None, info)."""
+    -> (mll, grad (numpy, d + 2), grad_X or None, U or None, info).  min_iter: CG
+    iterations run before the tolerance is tested (a loose tolerance such as the
+    training loop's 1.0 is otherwise met by x_0 = 0)."""
     import torch
     N, d = X.shape
     M = Z.shape[0]
     R = M + 1
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    opts = _CgOpts(float(tol), int(max_iter), 0, prec, CG_STABLE, REORTH_PINV, 1, 0, int(restarts),
+    opts = _CgOpts(float(tol), int(max_iter), int(min_iter), prec, CG_STABLE, REORTH_PINV, 1, 0, int(restarts),
                    PRECISIONS[check_precision] if isinstance(check_precision, str) else int(check_precision),
                    1 if escalate else 0)
     h = hyp.c()
