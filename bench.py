@@ -4,7 +4,8 @@ Workload (one "step"): N = 65,536 standardised Gaussian points in d = 8, RBF
 kernel (l = 1, a^2 = 1, sigma^2 = 0.05), B = [y, 16 Rademacher probes]
 (17 right-hand sides), rank-100 pivoted-Cholesky preconditioner, then the
 stable CG (Alg. 2) with FP16 tensor-core MVMs until every column's
-relative residual, recomputed with an FP32 MVM, is <= 1e-2.  The step is the
+relative residual, recomputed with an FP32 MVM, is <= 1e-2; the residual is
+verified in FP64 on sampled rows.  The step is the
 whole hot path: operand preparation, preconditioner factor + core, every MVM,
 Woodbury apply, LSE scalars, re-orthogonalisation, residual checks.
 

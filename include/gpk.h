@@ -234,11 +234,16 @@ typedef struct {
                             (fresh basis); at most this many times.  0 = trust the
                             recursive residual (re-orthogonalisation changes r but not
                             x, so the two drift apart by rounding)                   */
-    int check_precision; /* GP_PREC_* of the MVM that recomputes r = K x - b at a
-                            true-residual check.  GP_PREC_FP32 turns the restarts into
-                            mixed-precision iterative refinement: a half-precision MVM
-                            cannot resolve the residual of its own solution when
-                            K x cancels heavily (|x| >> |b| for small sigma^2)       */
+    int check_precision; /* GP_PREC_* (optionally | GP_MVM_* operand flags) of the MVM
+                            that recomputes r = K x - b at a true-residual check: the
+                            restarts become mixed-precision iterative refinement, since a
+                            single-rounded half-precision MVM cannot resolve the residual
+                            of its own solution when K x cancels heavily (|x| >> |b| for
+                            small sigma^2).  Use GP_PREC_FP32: the check's rounding error
+                            scales with sum_j |k_ij x_j|, which near the solution exceeds
+                            |(K x)_i| by the cancellation factor (hundreds on the bench
+                            workload), so even the hi + lo FP16 MVM (~1e-5) misreports
+                            a 1e-2 residual by ~10 %                                 */
     int escalate;        /* nonzero: when a run ends with a breakdown (a non-positive
                             d^T K d or r^T z: the low-precision operator is not positive
                             definite to the accuracy the solve has reached), the

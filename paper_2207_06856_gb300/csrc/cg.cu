@@ -374,7 +374,13 @@ int check_cg_args(const gp_hyp_t* hyp, int64_t N, int R, const gp_cg_opts_t* o) 
     if (o->max_iter < 1 || o->max_iter > 1000 || o->min_iter < 0 || !(o->tol >= 0.0)) return GP_ERR_INVALID;
     if (o->algorithm != GP_CG_STABLE && o->algorithm != GP_CG_STANDARD) return GP_ERR_INVALID;
     if (o->restarts < 0 || o->restarts > 16) return GP_ERR_INVALID;
-    if (o->check_precision < GP_PREC_FP32 || o->check_precision > GP_PREC_BF16) return GP_ERR_INVALID;
+    {
+        // the check MVM takes a precision and optionally the MVM's operand flags
+        const int cp = o->check_precision & 0xff;
+        const int known = 0xff | GP_MVM_XSPLIT | GP_MVM_NO_XSPLIT | GP_MVM_SCALE_SQRT_N | GP_MVM_VSPLIT |
+                          GP_MVM_BF16_SINGLE | GP_MVM_ONE_TILE | GP_MVM_PSPLIT;
+        if (cp < GP_PREC_FP32 || cp > GP_PREC_BF16 || (o->check_precision & ~known)) return GP_ERR_INVALID;
+    }
     if (o->reorth < GP_REORTH_NONE || o->reorth > GP_REORTH_EUCLID) return GP_ERR_INVALID;
     if (o->precision & GP_MVM_ADD_NOISE) return GP_ERR_INVALID;
     return GP_OK;
@@ -386,7 +392,7 @@ size_t cg_workspace(const Ctx* ctx, const gp_hyp_t* hyp, int64_t N, int R, int r
     WsCounter c;
     cg_layout(c, ctx, N, R, rank, o);
     size_t s = c.off + kop_workspace(ctx, hyp, N, N, R, o->precision, true);
-    if (o->restarts > 0 && o->check_precision != (o->precision & 0xff))
+    if (o->restarts > 0 && o->check_precision != o->precision)
         s += kop_workspace(ctx, hyp, N, N, R, o->check_precision, true);
     if (rank > 0) s += woodbury_workspace(ctx, N, rank, R);
     return s;
@@ -543,7 +549,7 @@ int CgSolver::setup(Ctx* c, WsCarver& wc, const gp_hyp_t* h, const float* X_, in
     if (rank > 0) GPK_TRY(woodbury_prepare(ctx, pc.core, rank, b.cinv, s));
     GPK_TRY(kop_prepare(ctx, wc, op, &hyp, X, N, X, N, R, o.precision, s));
     op_chk = &op;
-    if (o.restarts > 0 && o.check_precision != (o.precision & 0xff)) {
+    if (o.restarts > 0 && o.check_precision != o.precision) {
         GPK_TRY(kop_prepare(ctx, wc, op_chk_own, &hyp, X, N, X, N, R, o.check_precision, s));
         op_chk = &op_chk_own;
     }

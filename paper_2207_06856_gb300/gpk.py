@@ -48,6 +48,10 @@ MVM_ONE_TILE = 0x4000
 MVM_PSPLIT = 0x8000
 
 
+def _check_flags(check_precision, prec: int) -> int:
+    return PRECISIONS[check_precision] if isinstance(check_precision, str) else int(check_precision)
+
+
 class GPKError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -360,8 +364,7 @@ def cg_solve(ctx: Context, hyp: Hyper, X, B, precond: Precond | None = None, tol
     opts = _CgOpts(float(tol), int(max_iter), int(min_iter), prec,
                    CG_STABLE if algorithm == "stable" else CG_STANDARD,
                    REORTH[reorth] if isinstance(reorth, str) else int(reorth), int(reorth_passes),
-                   1 if U is not None else 0, int(restarts),
-                   PRECISIONS[check_precision] if isinstance(check_precision, str) else int(check_precision),
+                   1 if U is not None else 0, int(restarts), _check_flags(check_precision, prec),
                    1 if escalate else 0)
     h = hyp.c()
     rank = precond.rank if precond is not None else 0
@@ -473,8 +476,7 @@ def mll_and_grad(ctx: Context, hyp: Hyper, X, y, Z, precond: Precond | None = No
     R = M + 1
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     opts = _CgOpts(float(tol), int(max_iter), int(min_iter), prec, CG_STABLE, REORTH_PINV, 1, 0, int(restarts),
-                   PRECISIONS[check_precision] if isinstance(check_precision, str) else int(check_precision),
-                   1 if escalate else 0)
+                   _check_flags(check_precision, prec), 1 if escalate else 0)
     h = hyp.c()
     rank = precond.rank if precond is not None else 0
     need = int(lib().gp_mll_workspace_size(ctypes.byref(h), N, M, rank, ctypes.byref(opts)))
