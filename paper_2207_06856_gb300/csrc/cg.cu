@@ -14,11 +14,12 @@
 //
 // LSE.  The paper's transformation log w^T z = y_max + log sum s_i
 // exp(y_i - y_max), y_i = log|w_i| + log|z_i|, holds for any shift.  The GPU
-// takes the shift as a power of two: each FP32 x FP32 product is exact in
-// FP64, every thread keeps (e, s) with |p| 2^-e < 1 and s = sum p 2^-e,
-// partial pairs are merged in a fixed order, and LSE = log(s) + e log 2.  No
-// per-element transcendental is needed and nothing can overflow or
-// underflow.  A non-positive s is a breakdown of that column.
+// takes the shift as a power of two: each thread sums its FP32 x FP32
+// products exactly as float-float pairs, converts the pair to (e, s) with
+// |s| < 1 and partial sum = s 2^e in FP64, partial pairs are merged in a
+// fixed order, and LSE = log(s) + e log 2.  No per-element transcendental is
+// needed and nothing can overflow or underflow.  A non-positive s is a
+// breakdown of that column.
 //
 // Re-orthogonalisation.  In PCG the residuals are mutually orthogonal in the
 // P^{-1} inner product, so the default stores rho_j = r_j / sqrt(gamma_j),
@@ -78,6 +79,20 @@ __device__ __forceinline__ Lse lse_shfl(const Lse& a, int o) {
     return b;
 }
 
+// (hi, lo) += a * b exactly up to float-float rounding: TwoProd via FMA, then
+// Knuth's TwoSum of hi with the product's high part and a plain add of the
+// low parts.  Explicit round-to-nearest operations keep the compiler from
+// contracting or reassociating the error terms.
+__device__ __forceinline__ void ff_add_prod(float& hi, float& lo, float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float pe = __fmaf_rn(a, b, -p);          // a * b = p + pe exactly
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float se = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));   // hi + p = s + se
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(se, pe));
+}
+
 // part[(c * nblk + blk) * 3 + {0,1,2}] = (s, e, sum a^2) of column c over this chunk.
 __global__ void __launch_bounds__(kDotThreads)
 dots_kernel(const float* __restrict__ A, const float* __restrict__ B, int64_t N, int nblk,
@@ -86,22 +101,25 @@ dots_kernel(const float* __restrict__ A, const float* __restrict__ B, int64_t N,
     if (active && !active[c]) return;
     const float* a = A + (int64_t)c * N;
     const float* b = B + (int64_t)c * N;
-    // Each thread's 8 products are exact in FP64 and summed there (no FP32
-    // product can overflow or underflow FP64); the (s, e) form starts at the
-    // thread partial, which saves the per-element exponent work.
-    double sp = 0.0, n2 = 0.0;
+    // Each thread's 8 products are formed exactly as float-float pairs
+    // (TwoProd with an FMA) and summed with TwoSum on the FP32 pipe (FP64
+    // arithmetic is scarce on this GPU); the (hi, lo) partial then enters the
+    // FP64 (s, e) form.  Equivalent to an FP64 sum of the exact products up to
+    // the 48-bit significand of the pair (and FP32 range: |products| < 2^127).
+    float sh = 0.0f, sl = 0.0f, nh = 0.0f, nl = 0.0f;
     const int64_t base = (int64_t)blockIdx.x * kDotChunk;
 #pragma unroll
     for (int q = 0; q < kDotPerThread; ++q) {
         const int64_t i = base + q * kDotThreads + threadIdx.x;
         if (i < N) {
-            const double av = a[i], bv = b[i];
-            sp = fma(av, bv, sp);
-            n2 = fma(av, av, n2);
+            const float av = a[i], bv = b[i];
+            ff_add_prod(sh, sl, av, bv);
+            ff_add_prod(nh, nl, av, av);
         }
     }
     Lse acc{0.0, kEmptyExp};
-    lse_add(acc, sp);
+    lse_add(acc, (double)sh + (double)sl);
+    double n2 = (double)nh + (double)nl;
     for (int o = 16; o > 0; o >>= 1) {
         lse_merge(acc, lse_shfl(acc, o));
         n2 += __shfl_xor_sync(0xffffffffu, n2, o);
@@ -131,7 +149,8 @@ enum ScalarMode { SC_INIT = 0, SC_ALPHA = 1, SC_BETA = 2, SC_BNORM = 3 };
 // order, then run the scalar step of Alg. 1 / Alg. 2.
 __global__ void scalar_kernel(int mode, int stable, const double* __restrict__ part, int nblk, int R,
                               ColState* __restrict__ st, int k, double tol, int min_iter, double* __restrict__ ahist,
-                              double* __restrict__ bhist, double* __restrict__ rhist, int* __restrict__ n_active) {
+                              double* __restrict__ bhist, double* __restrict__ rhist, int* __restrict__ n_active,
+                            int* __restrict__ aflags) {
     __shared__ int cnt;
     if (threadIdx.x == 0) cnt = 0;
     __syncthreads();
@@ -206,6 +225,7 @@ __global__ void scalar_kernel(int mode, int stable, const double* __restrict__ p
                 if (S.breakdown && n_active) atomicAdd(&n_active[1], 1);   // breakdowns of this run
             }
         }
+        if (l == 0 && aflags) aflags[c] = S.active;   // the masks of the masked kernels
     }
     __syncthreads();
     if (threadIdx.x == 0 && n_active) *n_active = cnt;
@@ -250,9 +270,15 @@ __global__ void update_d_kernel(float* __restrict__ d, const float* __restrict__
     const int c = blockIdx.y;
     const ColState& S = st[c];
     if (!S.active) return;
-    const float beta = first ? 0.0f : (float)S.beta;
-    const float sg = (reorth == GP_REORTH_PINV) ? (float)(1.0 / sqrt(S.gamma))
-                                                : (float)(S.rnorm > 0.0 ? 1.0 / S.rnorm : 0.0);
+    // the column's scalars once per block: FP64 is slow on this GPU
+    __shared__ float s_beta, s_sg;
+    if (threadIdx.x == 0) {
+        s_beta = first ? 0.0f : (float)S.beta;
+        s_sg = (reorth == GP_REORTH_PINV) ? (float)(1.0 / sqrt(S.gamma))
+                                          : (float)(S.rnorm > 0.0 ? 1.0 / S.rnorm : 0.0);
+    }
+    __syncthreads();
+    const float beta = s_beta, sg = s_sg;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t o = (int64_t)c * N + i;
         const float zi = z[o];
@@ -327,11 +353,6 @@ __global__ void reorth_update_kernel(const float* __restrict__ RB, int nb, int R
     }
 }
 
-// The active flags of the Woodbury kernels, as a plain int array.
-__global__ void active_flags_kernel(const ColState* __restrict__ st, int R, int* __restrict__ flags) {
-    const int c = threadIdx.x;
-    if (c < R) flags[c] = st[c].active;
-}
 
 
 int vec_grid(const Ctx* ctx, int64_t N) {
@@ -429,11 +450,7 @@ int CgSolver::precond(const float* W, float* Z, bool masked) {
         copy_active_kernel<<<gcol, 256, 0, s>>>(Z, W, N, masked ? b.st : nullptr);
         return launched(1);
     }
-    if (masked) {
-        active_flags_kernel<<<1, 64, 0, s>>>(b.st, R, b.aflags);
-        GPK_TRY(launched(1));
-    }
-    WsCarver wtmp = wc_rest;   // Woodbury scratch beyond the solver's buffers
+    WsCarver wtmp = wc_rest;   // Woodbury scratch; the active flags come from the last scalar step
     return woodbury_apply(ctx, wtmp, pc.L, pc.core, b.cinv, rank, hyp.noise, N, W, R, masked ? b.aflags : nullptr,
                           Z, s);
 }
@@ -446,7 +463,7 @@ int CgSolver::dots(const float* A, const float* Bv, bool masked) {
 
 int CgSolver::scalar(int mode, int kk) {
     scalar_kernel<<<1, 1024, 0, s>>>(mode, stable, b.dpart, b.nblk_dot, R, b.st, kk, o.tol, o.min_iter, b.ahist,
-                                     b.bhist, b.rhist, b.nact);
+                                     b.bhist, b.rhist, b.nact, b.aflags);
     return launched(1);
 }
 
@@ -476,9 +493,7 @@ int CgSolver::iterate() {
     const size_t NR = (size_t)N * R;
     // Kd = Ktilde d
     GPK_TRY(kop_apply(ctx, escalated ? *op_chk : op, b.d, R, b.Kd, N, true, s));
-    active_flags_kernel<<<1, 64, 0, s>>>(b.st, R, b.aflags);
-    GPK_TRY(launched(1));
-    GPK_TRY(dots(b.d, b.Kd, true));
+    GPK_TRY(dots(b.d, b.Kd, true));   // masked by the flags of the last scalar step
     GPK_TRY(scalar(SC_ALPHA, k));
     update_xr_kernel<<<gcol, 256, 0, s>>>(U, b.r, b.d, b.Kd, N, b.st);
     GPK_TRY(launched(1));
