@@ -353,6 +353,7 @@ wb_out_kernel(const float* __restrict__ L, int64_t N, int k, const float* __rest
         float acc[RB];
 #pragma unroll
         for (int cc = 0; cc < RB; ++cc) acc[cc] = 0.0f;
+#pragma unroll 4
         for (int a = 0; a < k; ++a) {
             const float la = L[(int64_t)a * N + i];
 #pragma unroll
@@ -469,7 +470,8 @@ int pivchol_run(Ctx* ctx, WsCarver& wc, const gp_hyp_t* hyp, const float* X, int
 // ---- Woodbury apply ----
 namespace {
 int ltw_grid(const Ctx* ctx, int64_t N, int64_t* rows_per) {
-    const int64_t G = 2 * (int64_t)(ctx->num_sms > 0 ? ctx->num_sms : 148);
+    // several CTAs per SM: each walks its rows in dependent 32-row tiles
+    const int64_t G = 6 * (int64_t)(ctx->num_sms > 0 ? ctx->num_sms : 148);
     int64_t rp = (N + G - 1) / G;
     rp = ((rp + kLtwTile - 1) / kLtwTile) * kLtwTile;
     if (rp < kLtwTile) rp = kLtwTile;
