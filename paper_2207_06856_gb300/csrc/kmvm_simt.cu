@@ -27,8 +27,10 @@ kmvm_simt_kernel(const float* __restrict__ Xr, const float* __restrict__ Xc, con
                  int64_t Nr, int64_t Nc, int dp, int R, int n_split, float a2, float noise,
                  const float* __restrict__ Vnoise, float* __restrict__ out, int64_t ld_out,
                  float* __restrict__ partial, int64_t ld_part) {
-    __shared__ float sx[kSimtTile][DPM];
-    __shared__ float sv[kSimtTile][RPM];
+    // staged column tile; rows padded by 4 floats (16-byte aligned float4 reads,
+    // fewer bank conflicts on the transposing stores of V)
+    __shared__ __align__(16) float sx[kSimtTile][DPM + 4];
+    __shared__ __align__(16) float sv[kSimtTile][RPM + 4];
     const int tid = threadIdx.x;
     const int64_t i0 = (int64_t)blockIdx.x * kSimtRows + tid;
     const int64_t i1 = i0 + kSimtThreads;
@@ -62,10 +64,11 @@ kmvm_simt_kernel(const float* __restrict__ Xr, const float* __restrict__ Xc, con
 #pragma unroll
             for (int k = 0; k < DPM; k += 4) {
                 if (k < dp) {
+                    const float4 x4 = *reinterpret_cast<const float4*>(&sx[jj][k]);   // broadcast
+                    const float xj[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk) {
-                        const float xj = sx[jj][k + kk];
-                        const float d0 = x0[k + kk] - xj, d1 = x1[k + kk] - xj;
+                        const float d0 = x0[k + kk] - xj[kk], d1 = x1[k + kk] - xj[kk];
                         q0 = fmaf(d0, d0, q0);
                         q1 = fmaf(d1, d1, q1);
                     }
@@ -76,11 +79,12 @@ kmvm_simt_kernel(const float* __restrict__ Xr, const float* __restrict__ Xc, con
 #pragma unroll
             for (int c = 0; c < RPM; c += 4) {
                 if (c < R) {
+                    const float4 v4 = *reinterpret_cast<const float4*>(&sv[jj][c]);   // broadcast
+                    const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
                     for (int cc = 0; cc < 4; ++cc) {
-                        const float v = sv[jj][c + cc];
-                        acc0[c + cc] = fmaf(k0, v, acc0[c + cc]);
-                        acc1[c + cc] = fmaf(k1, v, acc1[c + cc]);
+                        acc0[c + cc] = fmaf(k0, vv[cc], acc0[c + cc]);
+                        acc1[c + cc] = fmaf(k1, vv[cc], acc1[c + cc]);
                     }
                 }
             }
