@@ -194,3 +194,53 @@ def test_precision_workload_full_size_fp16(ctx):
     est = np.sqrt(w.N / n * np.sum(r * r, axis=0)) / np.linalg.norm(Bt, axis=0)
     assert est.max() <= 1.1 * w.tol, est
     assert np.all(np.abs(est / reported - 1.0) <= 0.10), (est, reported)
+
+
+def test_breakdown_escalates_to_check_precision(ctx):
+    """N = 20,000 points in d = 2, RBF l = 0.5, sigma^2 = 1e-4, single-term FP16
+    inputs: the FP16 operator is not positive definite to the accuracy the solve
+    needs, so CG breaks down; with escalation (the default) the restart continues
+    with the FP32 check MVM and the solve converges by that MVM.  At this
+    conditioning |x| ~ |y| / sigma^2, and the FP32 check's rounding (proportional
+    to sum_j |k_ij x_j|) resolves the residual only to a few 1e-2: the FP64
+    residual is checked against 5e-2."""
+    from paper_2207_06856_gb300 import gpk
+    rng = np.random.default_rng(0)
+    N, d = 20000, 2
+    X = rng.standard_normal((N, d)).astype(np.float32)
+    y = (np.sin(2 * np.pi * X.mean(1)) + 0.1 * rng.standard_normal(N)).astype(np.float32)
+    hyp = gpk.Hyper(gpk.RBF, np.full(d, 0.5, np.float32), 1.0, 1e-4)
+    Xd, B = _dev(X), _dev(y[None])
+    pc = gpk.pivchol(ctx, hyp, Xd, 20)
+    _, st0, info0 = gpk.cg_solve(ctx, hyp, Xd, B, pc, tol=1e-2, max_iter=1000, precision="fp16",
+                                 flags=gpk.MVM_NO_XSPLIT, escalate=False)
+    assert st0 == gpk.GP_ERR_BREAKDOWN and info0["breakdowns"] >= 1
+    U, st1, info1 = gpk.cg_solve(ctx, hyp, Xd, B, pc, tol=1e-2, max_iter=1000, precision="fp16",
+                                 flags=gpk.MVM_NO_XSPLIT, escalate=True)
+    assert st1 == gpk.GP_OK and info1["escalated"] == 1, info1["rel_resid"]
+    rows = np.sort(np.random.default_rng(1).choice(N, 2048, replace=False))
+    oh = O.Hyp("rbf", np.full(d, 0.5), 1.0, 1e-4)
+    r = O.kmvm_rows(X, rows, U.cpu().numpy().T.astype(np.float64), oh)[:, 0] - y[rows]
+    est = np.sqrt(N / len(rows) * np.sum(r * r)) / np.linalg.norm(y.astype(np.float64))
+    assert est <= 5e-2, est
+
+
+def test_split_fp16_solve_needs_fp32_iteration_count(ctx):
+    """FP16 tensor-core MVM with the kernel tile and inputs carried as hi + lo:
+    the stable CG needs at most 15 % more iterations than FP32 on the precision
+    workload's distribution (N = 16,384), and its residual is verified in FP64."""
+    from paper_2207_06856_gb300 import gpk
+    w = workloads.precision(N=16384)
+    hyp = gpk.Hyper(w.kernel, w.lengthscale, w.outputscale, w.noise)
+    X, B = _dev(w.X), _dev(w.rhs())
+    pc = gpk.pivchol(ctx, hyp, X, w.rank)
+    _, st32, i32 = gpk.cg_solve(ctx, hyp, X, B, pc, tol=w.tol, max_iter=w.max_iter, precision="fp32")
+    U, st16, i16 = gpk.cg_solve(ctx, hyp, X, B, pc, tol=w.tol, max_iter=w.max_iter, precision="fp16",
+                                flags=gpk.MVM_PSPLIT | gpk.MVM_XSPLIT)
+    assert st32 == gpk.GP_OK and st16 == gpk.GP_OK
+    assert i16["iters"] <= 1.15 * i32["iters"], (i16["iters"], i32["iters"])
+    rows = np.sort(np.random.default_rng(3).choice(w.N, 2048, replace=False))
+    Bt = w.rhs().T.astype(np.float64)
+    r = O.kmvm_rows(w.X, rows, U.cpu().numpy().T, _ohyp(w), add_noise=True) - Bt[rows]
+    est = np.sqrt(w.N / len(rows) * np.sum(r * r, axis=0)) / np.linalg.norm(Bt, axis=0)
+    assert est.max() <= 1.15 * w.tol, est
