@@ -93,6 +93,16 @@ __device__ __forceinline__ void ff_add_prod(float& hi, float& lo, float a, float
     lo = __fadd_rn(lo, __fadd_rn(se, pe));
 }
 
+// Float-float addition (a_hi, a_lo) += (b_hi, b_lo): TwoSum of the high parts,
+// low parts and the rounding error added (the pair is not renormalised).
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float bh, float bl) {
+    const float s = __fadd_rn(hi, bh);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+    hi = s;
+    lo = __fadd_rn(__fadd_rn(lo, bl), e);
+}
+
 // part[(c * nblk + blk) * 3 + {0,1,2}] = (s, e, sum a^2) of column c over this chunk.
 __global__ void __launch_bounds__(kDotThreads)
 dots_kernel(const float* __restrict__ A, const float* __restrict__ B, int64_t N, int nblk,
@@ -101,11 +111,11 @@ dots_kernel(const float* __restrict__ A, const float* __restrict__ B, int64_t N,
     if (active && !active[c]) return;
     const float* a = A + (int64_t)c * N;
     const float* b = B + (int64_t)c * N;
-    // Each thread's 8 products are formed exactly as float-float pairs
-    // (TwoProd with an FMA) and summed with TwoSum on the FP32 pipe (FP64
-    // arithmetic is scarce on this GPU); the (hi, lo) partial then enters the
-    // FP64 (s, e) form.  Equivalent to an FP64 sum of the exact products up to
-    // the 48-bit significand of the pair (and FP32 range: |products| < 2^127).
+    // The chunk's products are formed exactly as float-float pairs (TwoProd
+    // with an FMA) and reduced with TwoSum on the FP32 pipe, through the warp
+    // and the block in a fixed order (FP64 arithmetic is scarce on this GPU);
+    // only the block's pair enters the FP64 (s, e) form.  The pair carries a
+    // 48-bit significand; FP32 range bounds the chunk sums (|sum| < 2^127).
     float sh = 0.0f, sl = 0.0f, nh = 0.0f, nl = 0.0f;
     const int64_t base = (int64_t)blockIdx.x * kDotChunk;
 #pragma unroll
@@ -117,29 +127,28 @@ dots_kernel(const float* __restrict__ A, const float* __restrict__ B, int64_t N,
             ff_add_prod(nh, nl, av, av);
         }
     }
-    Lse acc{0.0, kEmptyExp};
-    lse_add(acc, (double)sh + (double)sl);
-    double n2 = (double)nh + (double)nl;
     for (int o = 16; o > 0; o >>= 1) {
-        lse_merge(acc, lse_shfl(acc, o));
-        n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+        const float h1 = __shfl_xor_sync(0xffffffffu, sh, o), l1 = __shfl_xor_sync(0xffffffffu, sl, o);
+        const float h2 = __shfl_xor_sync(0xffffffffu, nh, o), l2 = __shfl_xor_sync(0xffffffffu, nl, o);
+        ff_add(sh, sl, h1, l1);
+        ff_add(nh, nl, h2, l2);
     }
-    __shared__ double ss[kDotThreads / 32], sn[kDotThreads / 32];
-    __shared__ int se[kDotThreads / 32];
+    __shared__ float4 sw[kDotThreads / 32];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) { ss[w] = acc.s; se[w] = acc.e; sn[w] = n2; }
+    if (l == 0) sw[w] = make_float4(sh, sl, nh, nl);
     __syncthreads();
     if (threadIdx.x == 0) {
-        Lse t{ss[0], se[0]};
-        double tn = sn[0];
+        float4 t = sw[0];
         for (int q = 1; q < kDotThreads / 32; ++q) {
-            lse_merge(t, Lse{ss[q], se[q]});
-            tn += sn[q];
+            ff_add(t.x, t.y, sw[q].x, sw[q].y);
+            ff_add(t.z, t.w, sw[q].z, sw[q].w);
         }
+        Lse acc{0.0, kEmptyExp};
+        lse_add(acc, (double)t.x + (double)t.y);
         double* o = part + ((int64_t)c * nblk + blockIdx.x) * 3;
-        o[0] = t.s;
-        o[1] = (double)t.e;
-        o[2] = tn;
+        o[0] = acc.s;
+        o[1] = (double)acc.e;
+        o[2] = (double)t.z + (double)t.w;
     }
 }
 
@@ -172,15 +181,18 @@ __global__ void scalar_kernel(int mode, int stable, const double* __restrict__ p
                 n2 += __shfl_xor_sync(0xffffffffu, n2, off);
             }
             if (l == 0) {
+                // acc = (s, e) with LSE = log s + e log 2; Alg. 2's
+                // exp(LSE_1 - LSE_2) is formed as ldexp(s_1 / s_2, e_1 - e_2):
+                // the same quotient, no transcendental, no overflow.
                 const bool pos = acc.e != kEmptyExp && acc.s > 0.0;
-                const double lse = pos ? log(acc.s) + (double)acc.e * 0.6931471805599453 : -INFINITY;
                 const double val = pos ? ldexp(acc.s, acc.e) : 0.0;
                 if (mode == SC_BNORM) {
                     S.bnorm = sqrt(n2);
                 } else if (mode == SC_INIT) {
                     S.rnorm = sqrt(n2);
                     S.relres = S.bnorm > 0.0 ? S.rnorm / S.bnorm : 0.0;
-                    S.log_gamma = lse;
+                    S.gamma_s = pos ? acc.s : 0.0;
+                    S.gamma_e = pos ? acc.e : 0;
                     S.gamma = val;
                     S.gamma0 = val;
                     S.alpha = 0.0;
@@ -192,13 +204,13 @@ __global__ void scalar_kernel(int mode, int stable, const double* __restrict__ p
                     S.active = (work && pos) ? 1 : 0;
                     if (rhist) rhist[(int64_t)k * R + c] = S.relres;
                 } else if (mode == SC_ALPHA) {
-                    // alpha_k = gamma_k / d^T K d  (Alg. 2: in log scale)
+                    // alpha_k = gamma_k / d^T K d  (Alg. 2: from the LSE forms)
                     if (!pos) {
                         S.breakdown = 1;
                         S.active = 0;
                         S.alpha = 0.0;
                     } else {
-                        S.alpha = stable ? exp(S.log_gamma - lse) : S.gamma / val;
+                        S.alpha = stable ? ldexp(S.gamma_s / acc.s, S.gamma_e - acc.e) : S.gamma / val;
                     }
                     if (ahist) ahist[(int64_t)k * R + c] = S.alpha;
                 } else {   // SC_BETA
@@ -214,8 +226,9 @@ __global__ void scalar_kernel(int mode, int stable, const double* __restrict__ p
                         S.active = 0;
                         S.beta = 0.0;
                     } else {
-                        S.beta = stable ? exp(lse - S.log_gamma) : val / S.gamma;
-                        S.log_gamma = lse;
+                        S.beta = stable ? ldexp(acc.s / S.gamma_s, acc.e - S.gamma_e) : val / S.gamma;
+                        S.gamma_s = acc.s;
+                        S.gamma_e = acc.e;
                         S.gamma = val;
                         if (bhist) bhist[(int64_t)k * R + c] = S.beta;
                         if (S.relres <= tol && k + 1 >= min_iter) S.active = 0;

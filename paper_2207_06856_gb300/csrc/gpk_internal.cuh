@@ -221,15 +221,15 @@ size_t cg_workspace(const Ctx* ctx, const gp_hyp_t* hyp, int64_t N, int R, int r
 
 // Per-column state of the solver (device memory).
 struct ColState {
-    double log_gamma;   // log r^T z (both algorithms keep it; Alg. 1 also keeps gamma)
-    double gamma;
+    double gamma_s;     // r^T z = gamma_s 2^gamma_e (the LSE form: log r^T z = log gamma_s + gamma_e log 2)
+    double gamma;       // r^T z (Alg. 1)
     double alpha, beta;
     double bnorm, rnorm, relres;
     double gamma0;      // r_0^T z_0 (the SLQ quadrature weight ||P^{-1/2} r_0||^2)
     int active;
     int iters;
     int breakdown;
-    int pad;
+    int gamma_e;
 };
 
 struct CgBufs {
