@@ -330,6 +330,7 @@ def run_ours(args):
                                    f"rel. resid 1e-2 with FP32 residual checks",
                        "global_batch": R, "seq_len": N, "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "flushed between steps (256 MB write)"},
+            "solves_per_s": world / t_step,
             "iters": int(inf["iters"]), "restarts": int(inf["restarts"]),
             "final_rel_resid_max": float(np.max(inf["rel_resid"])),
             "fp64_rel_resid_sampled_max": None if resid is None else float(np.max(resid)),
