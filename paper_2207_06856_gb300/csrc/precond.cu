@@ -243,9 +243,13 @@ core_inverse_kernel(const double* __restrict__ core, int k, double* __restrict__
 
 // tpart[blk][a][c] = sum over this CTA's rows of L[a][i] W[c][i]: FP32
 // register blocks of 4 a x 4 c per thread over 32-row tiles staged in shared
-// memory (row-major, a or c fastest, float4 reads), stored as FP64.
+// memory (row-major, a or c fastest, float4 reads), stored as FP64.  The next
+// tile's global loads are issued into registers before the current tile is
+// multiplied, so the memory latency overlaps the arithmetic.
 constexpr int kLtwTile = 32;
-__global__ void __launch_bounds__(256)
+constexpr int kLtwMaxL = 16;   // prefetched L elements per thread: nab_pass <= 32
+constexpr int kLtwMaxW = 8;    // prefetched W elements per thread: R <= 64
+__global__ void __launch_bounds__(256, 3)
 wb_ltw_kernel(const float* __restrict__ L, int64_t N, int k, const float* __restrict__ W, int R,
               int64_t rows_per_blk, int nab_pass, double* __restrict__ tpart) {
     extern __shared__ float4 sh4[];
@@ -260,27 +264,46 @@ wb_ltw_kernel(const float* __restrict__ L, int64_t N, int k, const float* __rest
     const int64_t r1 = (r0 + rows_per_blk < N) ? r0 + rows_per_blk : N;
     const int ab = threadIdx.x % nab_pass, cb = threadIdx.x / nab_pass;
     const bool worker = cb < ncb;
+    const int nLe = 4 * nab_pass * kLtwTile, nWe = 4 * ncb * kLtwTile;
+    float pl[kLtwMaxL], pw[kLtwMaxW];
     for (int a0 = 0; a0 < k; a0 += 4 * nab_pass) {
         float acc[4][4];
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
             for (int y = 0; y < 4; ++y) acc[x][y] = 0.0f;
-        for (int64_t i0 = r0; i0 < r1; i0 += kLtwTile) {
-            __syncthreads();
-            // stage L[a0 .. a0 + 4 nab_pass)[i0 .. i0 + 32) as [row][a] and W as [row][c]
-            for (int e = threadIdx.x; e < 4 * nab_pass * kLtwTile; e += blockDim.x) {
+        auto fetch = [&](int64_t i0) {
+#pragma unroll
+            for (int q = 0; q < kLtwMaxL; ++q) {
+                const int e = threadIdx.x + q * 256;
                 const int aa = e / kLtwTile, ii = e % kLtwTile;
                 const int64_t i = i0 + ii;
-                const int a = a0 + aa;
-                sLf[ii * 4 * lstride + aa] = (i < r1 && a < k) ? L[(int64_t)a * N + i] : 0.0f;
+                pl[q] = (e < nLe && i < r1 && a0 + aa < k) ? L[(int64_t)(a0 + aa) * N + i] : 0.0f;
             }
-            for (int e = threadIdx.x; e < 4 * ncb * kLtwTile; e += blockDim.x) {
+#pragma unroll
+            for (int q = 0; q < kLtwMaxW; ++q) {
+                const int e = threadIdx.x + q * 256;
                 const int cc = e / kLtwTile, ii = e % kLtwTile;
                 const int64_t i = i0 + ii;
-                sWf[ii * 4 * wstride + cc] = (i < r1 && cc < R) ? W[(int64_t)cc * N + i] : 0.0f;
+                pw[q] = (e < nWe && i < r1 && cc < R) ? W[(int64_t)cc * N + i] : 0.0f;
+            }
+        };
+        if (r0 < r1) fetch(r0);
+        for (int64_t i0 = r0; i0 < r1; i0 += kLtwTile) {
+            __syncthreads();
+            // stage the prefetched tile as [row][a] and [row][c]
+#pragma unroll
+            for (int q = 0; q < kLtwMaxL; ++q) {
+                const int e = threadIdx.x + q * 256;
+                if (e < nLe) sLf[(e % kLtwTile) * 4 * lstride + e / kLtwTile] = pl[q];
+            }
+#pragma unroll
+            for (int q = 0; q < kLtwMaxW; ++q) {
+                const int e = threadIdx.x + q * 256;
+                if (e < nWe) sWf[(e % kLtwTile) * 4 * wstride + e / kLtwTile] = pw[q];
             }
             __syncthreads();
+            if (i0 + kLtwTile < r1) fetch(i0 + kLtwTile);   // next tile in flight during the products
             if (worker) {
 #pragma unroll 8
                 for (int ii = 0; ii < kLtwTile; ++ii) {
@@ -517,6 +540,7 @@ int woodbury_apply(Ctx* ctx, WsCarver& wc, const float* L, const double* core, c
     const int ncb = (R + 3) / 4;
     const int nab_all = (k + 3) / 4;
     int nab_pass = 256 / ncb;
+    if (nab_pass > 32) nab_pass = 32;   // the prefetch registers of wb_ltw_kernel
     if (nab_pass > nab_all) nab_pass = nab_all;
     const size_t sh1 = (size_t)kLtwTile * ((nab_pass + 1) + (ncb + 1)) * sizeof(float4);
     if (sh1 > 48 * 1024 &&
