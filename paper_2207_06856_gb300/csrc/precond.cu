@@ -359,11 +359,14 @@ wb_gemv_kernel(const double* __restrict__ cinv, const double* __restrict__ t, in
 // z[c][i] = inv_s2 w[c][i] - inv_s4 sum_a L[a][i] u[a][c]   (active columns only)
 // u staged in shared memory as [a][RB] (RB a multiple of 4: float4 reads,
 // the same address across the warp).
+// grid.y: column groups of RB (c0 = RB * blockIdx.y): more threads in flight
+// than one per row.
 template <int RB>
 __global__ void __launch_bounds__(256)
-wb_out_kernel(const float* __restrict__ L, int64_t N, int k, const float* __restrict__ W, int R, int c0,
+wb_out_kernel(const float* __restrict__ L, int64_t N, int k, const float* __restrict__ W, int R,
               const float* __restrict__ u, float inv_s2, float inv_s4, const int* __restrict__ active,
               float* __restrict__ Z) {
+    const int c0 = RB * (int)blockIdx.y;
     extern __shared__ float4 su4[];   // [k][RB / 4]
     float* su = reinterpret_cast<float*>(su4);
     const int rc = (R - c0) < RB ? (R - c0) : RB;
@@ -556,19 +559,14 @@ int woodbury_apply(Ctx* ctx, WsCarver& wc, const float* L, const double* core, c
     int64_t g = (N + 255) / 256;
     const int64_t cap = 4 * (int64_t)(ctx->num_sms > 0 ? ctx->num_sms : 148);
     if (g > cap) g = cap;
-    const int RB = R <= 8 ? 8 : (R <= 16 ? 16 : (R <= 24 ? 24 : 32));
-    for (int c0 = 0; c0 < R; c0 += RB) {
-        const size_t sh = (size_t)k * RB * sizeof(float);
-        if (RB == 8)
-            wb_out_kernel<8><<<(unsigned)g, 256, sh, s>>>(L, N, k, W, R, c0, u, inv_s2, inv_s4, active, Z);
-        else if (RB == 16)
-            wb_out_kernel<16><<<(unsigned)g, 256, sh, s>>>(L, N, k, W, R, c0, u, inv_s2, inv_s4, active, Z);
-        else if (RB == 24)
-            wb_out_kernel<24><<<(unsigned)g, 256, sh, s>>>(L, N, k, W, R, c0, u, inv_s2, inv_s4, active, Z);
-        else
-            wb_out_kernel<32><<<(unsigned)g, 256, sh, s>>>(L, N, k, W, R, c0, u, inv_s2, inv_s4, active, Z);
-        ctx->launches++;
-    }
+    const int RB = R <= 4 ? 4 : 8;
+    const dim3 grid((unsigned)g, (unsigned)((R + RB - 1) / RB));
+    const size_t sh = (size_t)k * RB * sizeof(float);
+    if (RB == 4)
+        wb_out_kernel<4><<<grid, 256, sh, s>>>(L, N, k, W, R, u, inv_s2, inv_s4, active, Z);
+    else
+        wb_out_kernel<8><<<grid, 256, sh, s>>>(L, N, k, W, R, u, inv_s2, inv_s4, active, Z);
+    ctx->launches++;
     return cudaGetLastError() == cudaSuccess ? GP_OK : GP_ERR_CUDA;
 }
 
