@@ -104,6 +104,14 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def solve_config(N: int, R: int, kernel: str, world: int) -> dict:
+    """The `config` of the solve workload, shared by both arms."""
+    return {"workload": f"precision: N={N} d=8 {kernel} l=1 a2=1 sigma2=0.05, 1+16 RHS (y + Rademacher), "
+                        "rank-100 pivoted Cholesky, stable CG (Alg. 2) to rel. resid 1e-2 with FP32 residual checks",
+            "global_batch": R, "seq_len": N, "parallelism": "replicas" if world > 1 else "single GPU",
+            "l2": "flushed between steps (256 MB write)"}
+
+
 def max_over_ranks(x: float, device=None) -> float:
     """The largest x over all ranks of the initialised process group (x itself
     when there is none).  Replicas are timed by their slowest member."""
@@ -131,9 +139,9 @@ def run_reference(args):
         return
     import oracle as O
     from paper_2207_06856_gb300 import workloads
-    w = workloads.precision()
+    w = workloads.precision(kernel={"rbf": workloads.RBF, "matern32": workloads.MATERN32}[args.kernel])
     B = w.rhs().T.astype(np.float64)
-    hyp = O.Hyp("rbf", w.lengthscale, w.outputscale, w.noise)
+    hyp = O.Hyp(args.kernel, w.lengthscale, w.outputscale, w.noise)
     rows_per_step = 512
     rng = np.random.default_rng(0)
     fp32_iters = args.ref_iters
@@ -156,8 +164,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_rows, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "precision: N=65536 d=8 RBF l=1 sigma2=0.05, 1+16 RHS, rank-100 pivoted Cholesky",
-                   "global_batch": 17, "seq_len": 65536, "parallelism": "none (host cores)"},
+        "config": solve_config(w.N, B.shape[1], args.kernel, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"FP64 matrix-free MVM of {rows_per_step} random rows x 65536 columns x 17 RHS "
                                    f"per step, extrapolated x{w.N // rows_per_step} rows x {fp32_iters} "
@@ -325,11 +332,7 @@ def run_ours(args):
             "metric": METRIC, "value": t_step, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-            "config": {"workload": f"precision: N={N} d=8 {args.kernel} l=1 a2=1 sigma2=0.05, 1+16 RHS "
-                                   f"(y + Rademacher), rank-100 pivoted Cholesky, stable CG (Alg. 2) to "
-                                   f"rel. resid 1e-2 with FP32 residual checks",
-                       "global_batch": R, "seq_len": N, "parallelism": "replicas" if world > 1 else "single GPU",
-                       "l2": "flushed between steps (256 MB write)"},
+            "config": solve_config(N, R, args.kernel, world),
             "solves_per_s": world / t_step,
             "iters": int(inf["iters"]), "restarts": int(inf["restarts"]),
             "final_rel_resid_max": float(np.max(inf["rel_resid"])),
