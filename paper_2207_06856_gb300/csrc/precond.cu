@@ -11,8 +11,8 @@
 // global argmax pass is needed; the kernel row is evaluated on the fly from
 // the scaled inputs (SIMT FP32, same kernel forms as the MVM).
 //
-// Core.  C = I + sigma^-2 L^T L is accumulated in FP64 from exact FP64
-// products and factored C = Lc Lc^T in FP64 by one CTA.
+// Core.  C = I + sigma^-2 L^T L is accumulated in FP64 from FP32 sums of
+// 64-row chunks and factored C = Lc Lc^T in FP64 by one CTA.
 //
 // Apply.  P^{-1} w = sigma^-2 w - sigma^-4 L C^{-1} L^T w: t = L^T w (FP32
 // within 256-row blocks, FP64 across blocks, fixed order), u = C^{-1} t by
@@ -146,7 +146,11 @@ __global__ void gram_ll_kernel(const float* __restrict__ L, int64_t N, int k, in
             sb[ii][cc] = (i < r1 && cb < k) ? L[(int64_t)cb * N + i] : 0.0f;
         }
         __syncthreads();
-        for (int ii = 0; ii < 64; ++ii) acc = fma((double)sa[ii][la], (double)sb[ii][lb], acc);
+        // 64 products in FP32, the chunk sums in FP64 (FP64 is scarce on this GPU)
+        float cs = 0.0f;
+#pragma unroll 16
+        for (int ii = 0; ii < 64; ++ii) cs = fmaf(sa[ii][la], sb[ii][lb], cs);
+        acc += (double)cs;
         __syncthreads();
     }
     if (a < k && b < k) partial[((int64_t)s * k + a) * k + b] = acc;
