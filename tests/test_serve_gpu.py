@@ -178,3 +178,29 @@ def test_request_bytes_is_exact_layout_and_monotone():
     assert f(0, 1024) == 0 and f(1000, 0) == 0
     bad = g.Hyper(g.RBF, np.ones(8, np.float32), 1.0, 0.0).c()   # noise must be > 0
     assert g.lib().gp_server_request_bytes(ctypes.byref(opts), ctypes.byref(bad), 1000, 1024) == 0
+
+
+@pytest.mark.gpu
+def test_wait_timeout_and_invalid_requests(gpk):
+    """A host wait that runs out raises TimeoutError and leaves the request
+    pending (a second wait returns its result); invalid submissions are refused
+    at submit without reaching the device; a one-slot server serialises."""
+    reqs = _requests(3, seed=21, n_min=20000, n_max=30000)
+    srv = gpk.Server(0, arena_bytes=2 << 30, max_slots=1, rank=20)
+    try:
+        futs = [srv.submit(_hyp(gpk, r), r.X, r.y, r.Xstar) for r in reqs]
+        with pytest.raises(TimeoutError):
+            futs[-1].result(timeout=1e-4)
+        outs = [f.result(timeout=120)[1] for f in futs]
+        assert all(st["status"] == gpk.GP_OK for st in outs)
+        assert srv.stats()["max_inflight"] == 1
+        for a, b in zip(outs, outs[1:]):
+            assert b["t_admit_ms"] >= a["t_done_ms"] - 1.0   # one slot: admitted after the previous finished
+        r = reqs[0]
+        with pytest.raises(gpk.GPKError) as e:                # noise must be > 0
+            srv.submit(gpk.Hyper(r.kernel, r.lengthscale, r.outputscale, 0.0), r.X, r.y, r.Xstar)
+        assert e.value.status == gpk.GP_ERR_INVALID
+        with pytest.raises(ValueError):                       # X_test with the wrong d
+            srv.submit(_hyp(gpk, r), r.X, r.y, r.Xstar[:, :-1])
+    finally:
+        srv.close()
