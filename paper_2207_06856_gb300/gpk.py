@@ -328,7 +328,7 @@ class Precond:
         return _Precond(int(self.L.data_ptr()), int(self.core.data_ptr()), int(self.rank))
 
 
-def pivchol(ctx: Context, hyp: Hyper, X, rank: int, stream=None) -> Precond:
+def pivchol_precond(ctx: Context, hyp: Hyper, X, rank: int, stream=None) -> Precond:
     """gp_pivchol_precond: rank-k pivoted Cholesky of K(X, X) and its FP64 Woodbury core."""
     import torch
     N, d = X.shape
@@ -610,3 +610,7 @@ class Server:
         except Exception:
             pass
 
+
+
+# the C entry points' names (without the gp_ prefix) for every call of the boundary
+pivchol = pivchol_precond
