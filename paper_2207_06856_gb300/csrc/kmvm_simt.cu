@@ -10,6 +10,12 @@
 // threads read the same column: broadcast, no bank conflicts).  Column ranges
 // are split across blockIdx.y so the grid fills the 152 SMs many times over;
 // split partials are summed by launch_split_reduce in a fixed order.
+//
+// The arithmetic runs on packed FP32 pairs (__fadd2_rn / __ffma2_rn, two
+// IEEE round-to-nearest operations per instruction): a row's squared distance
+// as two interleaved partial sums over even and odd dimensions, and its
+// accumulators as pairs of adjacent output columns.  Shared memory holds the
+// negated column inputs so the difference is one packed add.
 #include "gpk_internal.cuh"
 #include "kfun.cuh"
 
@@ -28,20 +34,21 @@ kmvm_simt_kernel(const float* __restrict__ Xr, const float* __restrict__ Xc, con
                  const float* __restrict__ Vnoise, float* __restrict__ out, int64_t ld_out,
                  float* __restrict__ partial, int64_t ld_part) {
     // staged column tile; rows padded by 4 floats (16-byte aligned float4 reads,
-    // fewer bank conflicts on the transposing stores of V)
+    // fewer bank conflicts on the transposing stores of V).  sx holds -x_j.
     __shared__ __align__(16) float sx[kSimtTile][DPM + 4];
     __shared__ __align__(16) float sv[kSimtTile][RPM + 4];
     const int tid = threadIdx.x;
     const int64_t i0 = (int64_t)blockIdx.x * kSimtRows + tid;
     const int64_t i1 = i0 + kSimtThreads;
-    float x0[DPM], x1[DPM], acc0[RPM], acc1[RPM];
+    float2 x0[DPM / 2], x1[DPM / 2], acc0[RPM / 2], acc1[RPM / 2];
 #pragma unroll
-    for (int k = 0; k < DPM; ++k) {
-        x0[k] = (i0 < Nr && k < dp) ? Xr[i0 * dp + k] : 0.0f;
-        x1[k] = (i1 < Nr && k < dp) ? Xr[i1 * dp + k] : 0.0f;
+    for (int h = 0; h < DPM / 2; ++h) {
+        const int k = 2 * h;   // dp is a multiple of 4, so k < dp covers k + 1 too
+        x0[h] = (i0 < Nr && k < dp) ? make_float2(Xr[i0 * dp + k], Xr[i0 * dp + k + 1]) : make_float2(0.0f, 0.0f);
+        x1[h] = (i1 < Nr && k < dp) ? make_float2(Xr[i1 * dp + k], Xr[i1 * dp + k + 1]) : make_float2(0.0f, 0.0f);
     }
 #pragma unroll
-    for (int c = 0; c < RPM; ++c) { acc0[c] = 0.0f; acc1[c] = 0.0f; }
+    for (int h = 0; h < RPM / 2; ++h) { acc0[h] = make_float2(0.0f, 0.0f); acc1[h] = make_float2(0.0f, 0.0f); }
 
     const int64_t ntiles = (Nc + kSimtTile - 1) / kSimtTile;
     const int64_t t0 = (ntiles * blockIdx.y) / n_split, t1 = (ntiles * (blockIdx.y + 1)) / n_split;
@@ -50,7 +57,7 @@ kmvm_simt_kernel(const float* __restrict__ Xr, const float* __restrict__ Xc, con
         for (int e = tid; e < kSimtTile * DPM; e += kSimtThreads) {
             const int jj = e / DPM, k = e % DPM;
             const int64_t j = jb + jj;
-            sx[jj][k] = (j < Nc && k < dp) ? Xc[j * dp + k] : 0.0f;
+            sx[jj][k] = (j < Nc && k < dp) ? -Xc[j * dp + k] : 0.0f;
         }
         for (int e = tid; e < kSimtTile * RPM; e += kSimtThreads) {
             const int c = e / kSimtTile, jj = e % kSimtTile;
@@ -60,32 +67,32 @@ kmvm_simt_kernel(const float* __restrict__ Xr, const float* __restrict__ Xc, con
         __syncthreads();
         const int jn = (int)((Nc - jb) < kSimtTile ? (Nc - jb) : kSimtTile);
         for (int jj = 0; jj < jn; ++jj) {
-            float q0 = 0.0f, q1 = 0.0f;
+            float2 q0 = make_float2(0.0f, 0.0f), q1 = make_float2(0.0f, 0.0f);
 #pragma unroll
             for (int k = 0; k < DPM; k += 4) {
                 if (k < dp) {
                     const float4 x4 = *reinterpret_cast<const float4*>(&sx[jj][k]);   // broadcast
-                    const float xj[4] = {x4.x, x4.y, x4.z, x4.w};
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const float d0 = x0[k + kk] - xj[kk], d1 = x1[k + kk] - xj[kk];
-                        q0 = fmaf(d0, d0, q0);
-                        q1 = fmaf(d1, d1, q1);
-                    }
+                    const float2 xa = make_float2(x4.x, x4.y), xb = make_float2(x4.z, x4.w);
+                    const float2 d0a = __fadd2_rn(x0[k / 2], xa), d0b = __fadd2_rn(x0[k / 2 + 1], xb);
+                    const float2 d1a = __fadd2_rn(x1[k / 2], xa), d1b = __fadd2_rn(x1[k / 2 + 1], xb);
+                    q0 = __ffma2_rn(d0a, d0a, q0);
+                    q1 = __ffma2_rn(d1a, d1a, q1);
+                    q0 = __ffma2_rn(d0b, d0b, q0);
+                    q1 = __ffma2_rn(d1b, d1b, q1);
                 }
             }
-            const float k0 = kernel_from_s<KIND>(-q0);
-            const float k1 = kernel_from_s<KIND>(-q1);
+            const float k0 = kernel_from_s<KIND>(-(q0.x + q0.y));
+            const float k1 = kernel_from_s<KIND>(-(q1.x + q1.y));
+            const float2 kk0 = make_float2(k0, k0), kk1 = make_float2(k1, k1);
 #pragma unroll
             for (int c = 0; c < RPM; c += 4) {
                 if (c < R) {
                     const float4 v4 = *reinterpret_cast<const float4*>(&sv[jj][c]);   // broadcast
-                    const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-                    for (int cc = 0; cc < 4; ++cc) {
-                        acc0[c + cc] = fmaf(k0, vv[cc], acc0[c + cc]);
-                        acc1[c + cc] = fmaf(k1, vv[cc], acc1[c + cc]);
-                    }
+                    const float2 va = make_float2(v4.x, v4.y), vb = make_float2(v4.z, v4.w);
+                    acc0[c / 2] = __ffma2_rn(kk0, va, acc0[c / 2]);
+                    acc1[c / 2] = __ffma2_rn(kk1, va, acc1[c / 2]);
+                    acc0[c / 2 + 1] = __ffma2_rn(kk0, vb, acc0[c / 2 + 1]);
+                    acc1[c / 2 + 1] = __ffma2_rn(kk1, vb, acc1[c / 2 + 1]);
                 }
             }
         }
@@ -94,21 +101,23 @@ kmvm_simt_kernel(const float* __restrict__ Xr, const float* __restrict__ Xc, con
 #pragma unroll
     for (int c = 0; c < RPM; ++c) {
         if (c < R) {
+            const float s0 = (c & 1) ? acc0[c / 2].y : acc0[c / 2].x;
+            const float s1 = (c & 1) ? acc1[c / 2].y : acc1[c / 2].x;
             if (n_split == 1) {
                 if (i0 < Nr) {
-                    float v = a2 * acc0[c];
+                    float v = a2 * s0;
                     if (noise != 0.0f) v = fmaf(noise, Vnoise[(int64_t)c * Nc + i0], v);
                     out[(int64_t)c * ld_out + i0] = v;
                 }
                 if (i1 < Nr) {
-                    float v = a2 * acc1[c];
+                    float v = a2 * s1;
                     if (noise != 0.0f) v = fmaf(noise, Vnoise[(int64_t)c * Nc + i1], v);
                     out[(int64_t)c * ld_out + i1] = v;
                 }
             } else {
                 float* pp = partial + ((int64_t)blockIdx.y * RPM + c) * ld_part;
-                if (i0 < Nr) pp[i0] = acc0[c];
-                if (i1 < Nr) pp[i1] = acc1[c];
+                if (i0 < Nr) pp[i0] = s0;
+                if (i1 < Nr) pp[i1] = s1;
             }
         }
     }
@@ -136,22 +145,15 @@ cudaError_t simt_dispatch_r(const SimtPlan& pl, int RPM, dim3 grid, const float*
                             const float* Vn, float* out, int64_t ld_out, float* part, int64_t ld_part,
                             cudaStream_t s) {
     switch (RPM) {
-        case 4:
-            kmvm_simt_kernel<KIND, DPM, 4><<<grid, kSimtThreads, 0, s>>>(Xr, Xc, V, Nr, Nc, pl.dp, R, pl.n_split, a2,
-                                                                         noise, Vn, out, ld_out, part, ld_part);
+#define GPK_SIMT_CASE(RP)                                                                                        \
+        case RP:                                                                                                 \
+            kmvm_simt_kernel<KIND, DPM, RP><<<grid, kSimtThreads, 0, s>>>(Xr, Xc, V, Nr, Nc, pl.dp, R, pl.n_split, \
+                                                                          a2, noise, Vn, out, ld_out, part,     \
+                                                                          ld_part);                              \
             break;
-        case 8:
-            kmvm_simt_kernel<KIND, DPM, 8><<<grid, kSimtThreads, 0, s>>>(Xr, Xc, V, Nr, Nc, pl.dp, R, pl.n_split, a2,
-                                                                         noise, Vn, out, ld_out, part, ld_part);
-            break;
-        case 16:
-            kmvm_simt_kernel<KIND, DPM, 16><<<grid, kSimtThreads, 0, s>>>(Xr, Xc, V, Nr, Nc, pl.dp, R, pl.n_split,
-                                                                          a2, noise, Vn, out, ld_out, part, ld_part);
-            break;
-        case 32:
-            kmvm_simt_kernel<KIND, DPM, 32><<<grid, kSimtThreads, 0, s>>>(Xr, Xc, V, Nr, Nc, pl.dp, R, pl.n_split,
-                                                                          a2, noise, Vn, out, ld_out, part, ld_part);
-            break;
+        GPK_SIMT_CASE(4) GPK_SIMT_CASE(8) GPK_SIMT_CASE(12) GPK_SIMT_CASE(16)
+        GPK_SIMT_CASE(20) GPK_SIMT_CASE(24) GPK_SIMT_CASE(28) GPK_SIMT_CASE(32)
+#undef GPK_SIMT_CASE
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -175,7 +177,7 @@ cudaError_t simt_dispatch(const SimtPlan& pl, dim3 grid, const float* Xr, const 
 SimtPlan simt_plan(const Ctx* ctx, int64_t Nr, int64_t Nc, int d, int R) {
     SimtPlan p;
     p.dp = ((d + 3) / 4) * 4;
-    p.R_pad = R <= 4 ? 4 : (R <= 8 ? 8 : (R <= 16 ? 16 : 32));
+    p.R_pad = ((R + 3) / 4) * 4;   // accumulators for the columns in use only (R <= 32)
     p.n_rowblk = (int)((Nr + kSimtRows - 1) / kSimtRows);
     const int64_t ntiles = (Nc + kSimtTile - 1) / kSimtTile;
     const int64_t target = (int64_t)(ctx->num_sms > 0 ? ctx->num_sms : 148) * 16;

@@ -196,7 +196,7 @@ int kop_apply(Ctx* ctx, KOp& op, const float* V, int R, float* out, int64_t ld_o
         const float* Vc = V + (int64_t)c0 * op.Nc;
         if (op.prec == GP_PREC_FP32) {
             SimtPlan pl = op.sp;
-            pl.R_pad = rc <= 4 ? 4 : (rc <= 8 ? 8 : (rc <= 16 ? 16 : 32));
+            pl.R_pad = ((rc + 3) / 4) * 4;   // <= the plan's, which sized the partial buffer
             GPK_TRY(launch_kmvm_simt(ctx, pl, a, op.a2, op.Xs_r, op.Xs_c, Vc, op.partial, s));
         } else {
             TcPlan pl = op.tp;

@@ -70,6 +70,18 @@ def test_kmvm_matches_oracle(ctx, prec, kern, shape):
     assert _colerr(got, _ref(X, V, kern, ls, a2, s2)) <= TOL[prec]
 
 
+@pytest.mark.parametrize("kern", [0, 1])
+@pytest.mark.parametrize("R", [3, 7, 10, 14, 19, 23, 27, 31, 45])
+def test_kmvm_fp32_every_column_padding(ctx, kern, R):
+    """The FP32 engine keeps accumulators for the columns in use rounded up to a
+    multiple of 4 (and chunks of 32 beyond that): every padding, and a second
+    chunk narrower than the first, against the oracle."""
+    N, d = 517, 5
+    X, V, _, ls, a2, s2 = workloads.random_problem(N, d, R, seed=7 * R + kern, kernel=kern)
+    got = _run(ctx, X, V, kern, ls, a2, s2, "fp32")
+    assert _colerr(got, _ref(X, V, kern, ls, a2, s2)) <= TOL["fp32"]
+
+
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
 @pytest.mark.parametrize("kern", [0, 1, 2])
 @pytest.mark.parametrize("shape", [(129, 4, 16), (700, 8, 17), (333, 18, 17), (257, 16, 33), (2048, 8, 64)])
