@@ -154,17 +154,18 @@ dots_kernel(const float* __restrict__ A, const float* __restrict__ B, int64_t N,
 
 enum ScalarMode { SC_INIT = 0, SC_ALPHA = 1, SC_BETA = 2, SC_BNORM = 3 };
 
-// One block, one warp per column: merge the partials of column c in a fixed
-// order, then run the scalar step of Alg. 1 / Alg. 2.
-__global__ void scalar_kernel(int mode, int stable, const double* __restrict__ part, int nblk, int R,
-                              ColState* __restrict__ st, int k, double tol, int min_iter, double* __restrict__ ahist,
-                              double* __restrict__ bhist, double* __restrict__ rhist, int* __restrict__ n_active,
-                            int* __restrict__ aflags) {
-    __shared__ int cnt;
-    if (threadIdx.x == 0) cnt = 0;
-    __syncthreads();
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    for (int c = w; c < R; c += (blockDim.x >> 5)) {
+// One block of one warp per column, so the FP64 merges and recurrences of the
+// columns run on different SMs (FP64 throughput is per SM and low on this
+// GPU): merge the partials of column c in a fixed order, then run the scalar
+// step of Alg. 1 / Alg. 2.  The last block to finish counts the active
+// columns (n_active[2] is its ticket, returned to 0 by that block).
+__global__ void __launch_bounds__(32)
+scalar_kernel(int mode, int stable, const double* __restrict__ part, int nblk, int R, ColState* __restrict__ st,
+              int k, double tol, int min_iter, double* __restrict__ ahist, double* __restrict__ bhist,
+              double* __restrict__ rhist, int* __restrict__ n_active, int* __restrict__ aflags) {
+    const int l = threadIdx.x;
+    {
+        const int c = blockIdx.x;
         ColState& S = st[c];
         const bool act = (mode == SC_INIT || mode == SC_BNORM) ? true : (S.active != 0);
         if (act) {
@@ -234,14 +235,28 @@ __global__ void scalar_kernel(int mode, int stable, const double* __restrict__ p
                         if (S.relres <= tol && k + 1 >= min_iter) S.active = 0;
                     }
                 }
-                if (S.active) atomicAdd(&cnt, 1);
                 if (S.breakdown && n_active) atomicAdd(&n_active[1], 1);   // breakdowns of this run
             }
         }
         if (l == 0 && aflags) aflags[c] = S.active;   // the masks of the masked kernels
     }
-    __syncthreads();
-    if (threadIdx.x == 0 && n_active) *n_active = cnt;
+    if (n_active) {
+        int last = 0;
+        if (l == 0) {
+            __threadfence();
+            last = atomicAdd(&n_active[2], 1) == (int)gridDim.x - 1;
+        }
+        if (__shfl_sync(0xffffffffu, last, 0)) {
+            __threadfence();
+            int cnt = 0;
+            for (int q = l; q < R; q += 32) cnt += *(volatile const int*)&st[q].active != 0;
+            cnt = __reduce_add_sync(0xffffffffu, cnt);
+            if (l == 0) {
+                n_active[0] = cnt;
+                n_active[2] = 0;
+            }
+        }
+    }
 }
 
 // x += alpha d; r += alpha Kd   (active columns)
@@ -475,7 +490,7 @@ int CgSolver::dots(const float* A, const float* Bv, bool masked) {
 }
 
 int CgSolver::scalar(int mode, int kk) {
-    scalar_kernel<<<1, 1024, 0, s>>>(mode, stable, b.dpart, b.nblk_dot, R, b.st, kk, o.tol, o.min_iter, b.ahist,
+    scalar_kernel<<<(unsigned)R, 32, 0, s>>>(mode, stable, b.dpart, b.nblk_dot, R, b.st, kk, o.tol, o.min_iter, b.ahist,
                                      b.bhist, b.rhist, b.nact, b.aflags);
     return launched(1);
 }
@@ -516,7 +531,8 @@ int CgSolver::iterate() {
         for (int p = 0; p < passes; ++p) {
             gram_kernel<<<gdot, kDotThreads, (size_t)(kDotThreads / 32) * nb * sizeof(float), s>>>(
                 ZB, nb, R, b.r, N, b.nblk_dot, b.st, b.gpart);
-            gram_finalize_kernel<<<(nb * R + 255) / 256, 256, 0, s>>>(b.gpart, b.nblk_dot, nb, R, b.st, b.coef);
+            // 32-thread blocks: the FP64 sums spread over many SMs
+            gram_finalize_kernel<<<(nb * R + 31) / 32, 32, 0, s>>>(b.gpart, b.nblk_dot, nb, R, b.st, b.coef);
             reorth_update_kernel<<<gcol, 256, 0, s>>>(b.rho, nb, R, b.coef, b.r, N, b.st);
             GPK_TRY(launched(3));
         }
@@ -574,6 +590,7 @@ int CgSolver::setup(Ctx* c, WsCarver& wc, const gp_hyp_t* h, const float* X_, in
     b.len0 = wc.take<int>((size_t)R);
     b.cinv = rank > 0 ? wc.take<double>((size_t)rank * rank) : nullptr;
     if (!wc.ok) return GP_ERR_WORKSPACE;
+    GPK_CUDA_TRY(cudaMemsetAsync(b.nact, 0, 4 * sizeof(int), s));   // counts and the scalar step's ticket
     if (rank > 0) GPK_TRY(woodbury_prepare(ctx, pc.core, rank, b.cinv, s));
     GPK_TRY(kop_prepare(ctx, wc, op, &hyp, X, N, X, N, R, o.precision, s));
     op_chk = &op;

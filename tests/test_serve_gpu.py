@@ -37,10 +37,17 @@ def gpk():
 @pytest.mark.gpu
 def test_serve_fp32_matches_exact_posterior_mean(gpk):
     """FP32 MVMs, CG to 1e-6: mu* = K(X*, X) Ktilde^{-1} y against the oracle's
-    Cholesky solve (relative error <= 1e-4; FP64 CG to the same tolerance lands
-    within ~1e-6 on these requests)."""
+    Cholesky solve, within the first-order perturbation bound of the served
+    arithmetic: mu - mu_exact = K* Ktilde^{-1} r_true + dK* v with
+    ||r_true|| <= rel_resid ||y|| + ||dKtilde v||, where dKtilde v and dK* v are
+    the FP32 MVM's own errors (measured on the device at the exact weights v;
+    the reported residual is computed with the same FP32 operator, so it cannot
+    see them).  Factor 2: the solver meets those errors at its iterates, not at
+    v.  On these requests the bound is about 1e-4 relative."""
     srv = gpk.Server(0, arena_bytes=1 << 30, max_slots=4, rank=20, precision="fp32", mean_precision="fp32",
                      tol=1e-6, max_iter=600)
+    ctx = gpk.Context(0)
+    dev = torch.device("cuda:0")
     try:
         reqs = _requests(6, seed=3)
         futs = [srv.submit(_hyp(gpk, r), r.X, r.y, r.Xstar) for r in reqs]
@@ -48,11 +55,24 @@ def test_serve_fp32_matches_exact_posterior_mean(gpk):
             mean, st = f.result(timeout=120)
             assert st["status"] == gpk.GP_OK, st
             oh = _ohyp(r)
-            v = O.cholesky_solve(r.X, oh, r.y.astype(np.float64))
-            ref = O.kernel_matrix(r.Xstar, r.X, oh) @ v
-            err = np.linalg.norm(mean - ref) / np.linalg.norm(ref)
-            assert err <= 1e-4, (r.rid, r.X.shape, err)
+            Kt = O.ktilde_dense(r.X, oh)
+            Ks = O.kernel_matrix(r.Xstar, r.X, oh)
+            y = r.y.astype(np.float64)
+            v = np.linalg.solve(Kt, y)
+            ref = Ks @ v
+            A = np.linalg.solve(Kt, Ks.T).T          # K* Ktilde^{-1} (Ktilde symmetric)
+            Xd = torch.from_numpy(r.X).to(dev)
+            vd = torch.from_numpy(v.astype(np.float32)[None, :]).to(dev)
+            kv = gpk.kmvm(ctx, _hyp(gpk, r), Xd, vd, precision="fp32", add_noise=True).cpu().numpy()[0]
+            ksv = gpk.kmvm(ctx, _hyp(gpk, r), torch.from_numpy(r.Xstar).to(dev), vd, Xc=Xd, precision="fp32",
+                           add_noise=False).cpu().numpy()[0]
+            e_t = np.linalg.norm(kv - Kt @ v)
+            e_s = np.linalg.norm(ksv - ref)
+            bound = np.linalg.norm(A, 2) * (st["rel_resid"] * np.linalg.norm(y) + e_t) + e_s
+            err = np.linalg.norm(mean - ref)
+            assert err <= 2.0 * bound + 1e-6 * np.linalg.norm(ref), (r.rid, r.X.shape, err, bound)
     finally:
+        ctx.close()
         srv.close()
 
 
