@@ -500,8 +500,10 @@ int pivchol_run(Ctx* ctx, WsCarver& wc, const gp_hyp_t* hyp, const float* X, int
 // ---- Woodbury apply ----
 namespace {
 int ltw_grid(const Ctx* ctx, int64_t N, int64_t* rows_per) {
-    // several CTAs per SM: each walks its rows in dependent 32-row tiles
-    const int64_t G = 6 * (int64_t)(ctx->num_sms > 0 ? ctx->num_sms : 148);
+    // two CTAs per SM, each walking its rows in dependent 32-row tiles: more
+    // CTAs hide more latency but each adds k x R FP64 partials to reduce
+    // (measured on the precision workload: 2 per SM beat 3, 4 and 6)
+    const int64_t G = 2 * (int64_t)(ctx->num_sms > 0 ? ctx->num_sms : 148);
     int64_t rp = (N + G - 1) / G;
     rp = ((rp + kLtwTile - 1) / kLtwTile) * kLtwTile;
     if (rp < kLtwTile) rp = kLtwTile;
