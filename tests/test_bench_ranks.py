@@ -45,3 +45,39 @@ def test_max_over_ranks_gloo_two_ranks():
 def test_max_over_ranks_without_process_group():
     import bench
     assert bench.max_over_ranks(3.0) == 3.0
+
+
+def _bench(args, env_extra=None):
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, **(env_extra or {}))
+    r = subprocess.run([sys.executable, "bench.py", *args], cwd=root, env=env, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    return [json.loads(ln) for ln in lines]
+
+
+def test_reference_arm_prints_one_contract_line():
+    """`bench.py --impl reference` (the FP64 oracle on the host cores) prints one
+    JSON line with the solve arm's metric, unit, direction and config, a
+    cpu_baseline describing the run, and an e2e block with no transfers."""
+    import bench
+    out = _bench(["--impl", "reference", "--steps", "1", "--warmup", "0"])
+    assert len(out) == 1
+    d = out[0]
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["higher_is_better"] is False and d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] == 0
+    assert d["config"] == bench.solve_config(65536, 17, "rbf", 1)
+    assert d["value"] > 0 and d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    """Under a multi-rank launch only rank 0 runs the reference arm."""
+    out = _bench(["--impl", "reference", "--steps", "1", "--warmup", "0", "--gpus", "2"],
+                 {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert out == []
