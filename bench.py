@@ -281,6 +281,7 @@ def run_ours(args):
                                     ("bf16_stable_alg2", "bf16", "stable", "pinv"),
                                     ("fp16_split_tile_and_inputs_stable_alg2",
                                      gpk.FP16 | gpk.MVM_PSPLIT | gpk.MVM_XSPLIT, "stable", "pinv"),
+                                    ("fp16_half_exp_stable_alg2", gpk.FP16 | gpk.MVM_HALF_EXP, "stable", "pinv"),
                                     ("fp32_stable_alg2", "fp32", "stable", "pinv")]:
             ts, inf, _ = timed(prec, alg, ro, max(1, min(args.steps, 2)), 1)
             arms[name] = {"s_per_solve": float(np.mean(ts)), "iters": int(inf[-1]["iters"]),
@@ -364,7 +365,8 @@ def run_kmvm(args):
     X = torch.from_numpy(w.X).cuda()
     B = torch.from_numpy(w.rhs()).cuda()
     out = torch.empty_like(B)
-    fl = (gpk.MVM_ONE_TILE if args.one_tile else 0) | (gpk.MVM_PSPLIT if args.psplit else 0)
+    fl = (gpk.MVM_ONE_TILE if args.one_tile else 0) | (gpk.MVM_PSPLIT if args.psplit else 0) | \
+        (gpk.MVM_HALF_EXP if args.half_exp else 0)
     for _ in range(args.warmup):
         gpk.kmvm(ctx, hyp, X, B, precision=args.precision, add_noise=True, out=out, flags=fl)
     torch.cuda.synchronize()
@@ -383,6 +385,7 @@ def run_kmvm(args):
     pairs = float(w.N) ** 2
     print(json.dumps({"mode": "kmvm", "precision": args.precision, "kernel": args.kernel,
                       "engine": "one-tile" if args.one_tile else "pair", "psplit": bool(args.psplit),
+                      "half_exp": bool(args.half_exp),
                       "launches": n,
                       "avg_launch_ms": ms / max(n, 1), "pairs_per_s": pairs / (ms / max(n, 1) / 1e3)}), flush=True)
 
@@ -597,6 +600,7 @@ def main():
     ap.add_argument("--scale-n", type=int, default=1843200)
     ap.add_argument("--one-tile", action="store_true", help="kmvm mode: the one-row-tile tensor-core engine")
     ap.add_argument("--psplit", action="store_true", help="kmvm mode: FP16 kernel tile as hi + lo")
+    ap.add_argument("--half-exp", action="store_true", help="kmvm mode: FP16 exp2 argument and exponential")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-arena-gb", type=float, default=48.0)

@@ -88,6 +88,11 @@ extern "C" {
                                        bits; CG then needs about the FP32 iteration
                                        count, at about 1.5x the MVM time).  BF16
                                        does by default.                          */
+#define GP_MVM_HALF_EXP    0x10000  /* FP16 RBF: the exp2 argument rounded to FP16
+                                       by the tensor core and 2^s evaluated in
+                                       FP16 (ex2.approx.f16x2), the paper's
+                                       half-precision kernel evaluation (Sec. 4.1);
+                                       pair engine, d <= 12 without input split  */
 #define GP_MVM_ONE_TILE     0x4000  /* tensor-core MVM on the one-row-tile engine
                                        (P V with M = 128 rows, N = R) instead of
                                        the default pair engine (transposed

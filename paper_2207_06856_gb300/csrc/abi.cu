@@ -143,13 +143,7 @@ static int check_kmvm_args(const gp_hyp_t* hyp, int64_t Nr, int64_t Nc, int R, i
     GPK_TRY(check_hyp(hyp));
     if (Nr < 1 || Nc < 1 || Nr > (int64_t(1) << 31) - 256 || Nc > (int64_t(1) << 31) - 256) return GP_ERR_INVALID;
     if (R < 1 || R > 64) return GP_ERR_INVALID;
-    const int prec = flags & 0xff;
-    if (prec != GP_PREC_FP32 && prec != GP_PREC_FP16 && prec != GP_PREC_BF16) return GP_ERR_INVALID;
-    const int known = 0xff | GP_MVM_ADD_NOISE | GP_MVM_XSPLIT | GP_MVM_NO_XSPLIT | GP_MVM_SCALE_SQRT_N |
-                      GP_MVM_VSPLIT | GP_MVM_BF16_SINGLE | GP_MVM_ONE_TILE | GP_MVM_PSPLIT;
-    if (flags & ~known) return GP_ERR_INVALID;
-    if ((flags & GP_MVM_XSPLIT) && (flags & GP_MVM_NO_XSPLIT)) return GP_ERR_INVALID;
-    return GP_OK;
+    return check_mvm_flags(flags, true);
 }
 
 size_t gp_kmvm_workspace_size(const gp_hyp_t* hyp, int64_t Nr, int64_t Nc, int R, int flags) {

@@ -423,15 +423,10 @@ int check_cg_args(const gp_hyp_t* hyp, int64_t N, int R, const gp_cg_opts_t* o) 
     if (o->max_iter < 1 || o->max_iter > 1000 || o->min_iter < 0 || !(o->tol >= 0.0)) return GP_ERR_INVALID;
     if (o->algorithm != GP_CG_STABLE && o->algorithm != GP_CG_STANDARD) return GP_ERR_INVALID;
     if (o->restarts < 0 || o->restarts > 16) return GP_ERR_INVALID;
-    {
-        // the check MVM takes a precision and optionally the MVM's operand flags
-        const int cp = o->check_precision & 0xff;
-        const int known = 0xff | GP_MVM_XSPLIT | GP_MVM_NO_XSPLIT | GP_MVM_SCALE_SQRT_N | GP_MVM_VSPLIT |
-                          GP_MVM_BF16_SINGLE | GP_MVM_ONE_TILE | GP_MVM_PSPLIT;
-        if (cp < GP_PREC_FP32 || cp > GP_PREC_BF16 || (o->check_precision & ~known)) return GP_ERR_INVALID;
-    }
+    // the solve's and the check's MVM: a precision and optionally operand flags
+    GPK_TRY(check_mvm_flags(o->check_precision, false));
     if (o->reorth < GP_REORTH_NONE || o->reorth > GP_REORTH_EUCLID) return GP_ERR_INVALID;
-    if (o->precision & GP_MVM_ADD_NOISE) return GP_ERR_INVALID;
+    GPK_TRY(check_mvm_flags(o->precision, false));
     return GP_OK;
 }
 

@@ -88,6 +88,7 @@ struct OperandLayout {
     int k_pad = 0;   // 16, 32 or 64 (0: does not fit)
     int vsplit = 0;  // 1: right-hand sides carried as hi + lo (extra P.V product)
     int psplit = 0;  // 1: kernel tile carried as hi + lo (extra P.V product; BF16)
+    int half_exp = 0;  // 1: S rounded to FP16 by the MMA, 2^s in FP16 (RBF, FP16, k_pad 16)
 };
 OperandLayout make_layout(int d, int prec, int xsplit, int vsplit, int psplit);
 float kernel_input_scale(int kernel);   // c such that x_hat = c x / l
@@ -201,6 +202,9 @@ int encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, u
 
 // Hyperparameter validation shared by the entry points.
 int check_hyp(const gp_hyp_t* hyp);
+// MVM precision / option flags (GP_PREC_* | GP_MVM_*) accepted by every entry
+// point that takes them; GP_MVM_ADD_NOISE only where allow_noise.
+int check_mvm_flags(int flags, bool allow_noise);
 
 // ---- preconditioner (precond.cu) ----
 size_t pivchol_workspace(const Ctx* ctx, int64_t N, int d, int rank);

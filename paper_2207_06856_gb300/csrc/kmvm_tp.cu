@@ -32,8 +32,13 @@
 // Work item = (pair of 128-row tiles, column split).  Warps: 0-15 epilogue
 // (warpgroup q handles row tile q & 1, columns [64 (q >> 1), 64 (q >> 1) + 64):
 // four warps per scheduler hide the TMEM and shared-memory latencies behind the
-// special-function work), 16 TMA producer, 17 MMA issuer and TMEM owner.  TMEM: S of tile 0 [0,128), S of tile 1 [128,256), O^T
-// [256,512).  Shared memory: the X_j / Vt_j stage ring first, then the two
+// special-function work), 16 TMA producer, 17 S issuer and TMEM owner, 18
+// value-product issuer (one issuing warp serialises too many high-latency
+// tcgen05 and mbarrier operations per tile pair; see tp_mma_s).  TMEM: S of
+// tile 0 [0,128), S of tile 1 [128,256), O^T [256,512).  The epilogue signals
+// each barrier once per warp (after __syncwarp), never once per thread.
+// With HS (GP_MVM_HALF_EXP) the S product accumulates in FP16 and the
+// epilogue evaluates 2^s in FP16 pairs.  Shared memory: the X_j / Vt_j stage ring first, then the two
 // K-block P buffers (32 KB each, 64 KB with the hi + lo split), then the
 // row-tile buffers.  The A operand of the value
 // product spans 128 rows of which the first rv = R_pad (1 + vsplit) hold Vt;
@@ -58,9 +63,10 @@ constexpr int kBN = 128;
 constexpr int kPairRows = 256;
 constexpr int kMaxStages = 6;
 constexpr int kEpiWarps = 16;
-constexpr int kThreads = (kEpiWarps + 2) * 32;
+constexpr int kThreads = (kEpiWarps + 3) * 32;
 constexpr int kTmaWarp = kEpiWarps;
-constexpr int kMmaWarp = kEpiWarps + 1;
+constexpr int kMmaWarp = kEpiWarps + 1;   // S issuer, TMEM owner
+constexpr int kPvWarp = kEpiWarps + 2;    // value-product issuer
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kTmemO = 256;
 constexpr uint32_t kPKBlock = (uint32_t)kPairRows * 128u;   // one 64-column K-block of P: 256 rows x 128 B
@@ -89,7 +95,7 @@ struct TpBarriers {
     uint64_t o_empty;
     uint64_t xi_full[2];
     uint64_t xi_empty[2];
-    uint64_t drain;
+    uint64_t drain[2];      // per issuing warp
 };
 
 __device__ __forceinline__ void record_error(int* err, int code) { atomicCAS(err, 0, code); }
@@ -149,27 +155,31 @@ __device__ void tp_producer(const TpParams& p, const CUtensorMap* tmA, const CUt
     }
 }
 
-// ---- MMA issuer (one thread) ----------------------------------------------------
-// Event driven: S(t) for both row tiles once their S buffers have been read
-// and the stage has landed; the value product of K-block kb of tile t once
-// both row tiles' P columns of that K-block are in shared memory (and, first
-// in an item, O has been read out).
-template <int PSPLIT>
-__device__ void tp_mma(const TpParams& p, TpBarriers& bars, const uint8_t* sSt, const uint8_t* sP,
-                       const uint8_t* sXi, uint32_t xbytes, uint32_t vtbytes, uint32_t tmem, uint32_t id_s,
-                       uint32_t id_pv) {
+// ---- MMA issuers (two converged warps) ---------------------------------------------
+// Every tcgen05 operation, mbarrier probe and index step of an issuing warp has
+// a latency of the order of a hundred cycles, so one warp issuing both
+// products serialises about thirty of them per tile pair; split in two, the S
+// issuer re-issues S as soon as the epilogue has read it while the other warp
+// is still issuing the previous tile's value product.  Both warps run their
+// loops converged (every decision is warp-uniform) and issue each tcgen05.mma
+// and commit from one elected lane.  The tensor pipe executes what the two
+// warps issue in arrival order; S and O^T live in disjoint TMEM columns.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+    return __all_sync(0xffffffffu, ptx::mbar_wait(bar, parity, limit_ns));
+}
+
+// S issuer: for each column tile, S = XA_i XB_j^T for both row tiles once both
+// S buffers have been read (s_empty) and the stage has landed (full).
+__device__ void tp_mma_s(const TpParams& p, TpBarriers& bars, const uint8_t* sSt, const uint8_t* sXi,
+                         uint32_t xbytes, uint32_t vtbytes, uint32_t tmem, uint32_t id_s) {
     const uint32_t arow = (uint32_t)p.k_pad * 2u;                            // 32, 64 or 128 bytes
     const uint32_t swz = (arow == 32) ? 6u : (arow == 64 ? 4u : 2u);
     const int ksteps = p.k_pad / 16;
     const uint32_t S = (uint32_t)p.stages;
     const uint32_t aSt = ptx::smem_u32(sSt);
-    const uint32_t aP = ptx::smem_u32(sP);
     const uint32_t stage_bytes = xbytes + vtbytes;
-    const uint32_t kblk = (uint32_t)p.rv * 128u;
-    const long long limit = (long long)(p.limit_ns * 2ull);
     const uint32_t hi_x = ptx::smem_desc_hi(8u * arow, swz);
-    const uint32_t hi_128 = ptx::smem_desc_hi(1024u, 2u);
-    uint32_t n = 0, gt = 0;
+    uint32_t g = 0, st = 0, ph = 0;   // tiles issued; stage ring slot and its fill parity
     int ic = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x, ++ic) {
@@ -178,82 +188,85 @@ __device__ void tp_mma(const TpParams& p, TpBarriers& bars, const uint8_t* sSt, 
         const uint32_t T = (uint32_t)(j1 - j0);
         const int xb = p.xi_bufs == 2 ? (ic & 1) : 0;
         const int use = p.xi_bufs == 2 ? (ic >> 1) : ic;
-        if (!ptx::mbar_wait(&bars.xi_full[xb], use & 1, p.limit_ns)) { ok = false; break; }
+        if (!warp_wait(&bars.xi_full[xb], use & 1, p.limit_ns)) { ok = false; break; }
         ptx::tc_fence_after();
         const uint32_t aXi = ptx::smem_u32(sXi) + (uint32_t)xb * 2u * xbytes;
-        uint32_t ts = 0, tp = 0, tk = 0;
-        long long idle_since = clock64();
-        while (tp < T) {
-            bool progressed = false;
-            if (ts < T) {
-                const uint32_t g = gt + ts, f = n + ts, st = f % S;
-                const bool bufs_free = (g == 0) || (ptx::mbar_test(&bars.s_empty[0], (g - 1) & 1) &&
-                                                    ptx::mbar_test(&bars.s_empty[1], (g - 1) & 1));
-                if (bufs_free && ptx::mbar_test(&bars.full[st], (f / S) & 1)) {
-                    ptx::tc_fence_after();
-                    const uint32_t aXj = aSt + st * stage_bytes;
-                    for (int w = 0; w < 2; ++w) {
-                        for (int kk = 0; kk < ksteps; ++kk) {
-                            const uint32_t koff = (uint32_t)kk * 32u;
-                            ptx::mma_f16_ss(tmem + (uint32_t)w * 128u,
-                                            ptx::smem_desc_at(hi_x, aXi + (uint32_t)w * xbytes + koff),
-                                            ptx::smem_desc_at(hi_x, aXj + koff), id_s, kk > 0 ? 1u : 0u);
-                        }
-                        ptx::mma_commit(&bars.s_full[w]);
-                    }
-                    if (ts + 1 == T) ptx::mma_commit(&bars.xi_empty[xb]);   // last use of the row tiles
-                    ++ts;
-                    progressed = true;
+        for (uint32_t t = 0; t < T; ++t, ++g) {
+            if (g > 0 && !(warp_wait(&bars.s_empty[0], (g - 1) & 1, p.limit_ns) &&
+                           warp_wait(&bars.s_empty[1], (g - 1) & 1, p.limit_ns))) { ok = false; break; }
+            if (!warp_wait(&bars.full[st], ph, p.limit_ns)) { ok = false; break; }
+            ptx::tc_fence_after();
+            const uint32_t aXj = aSt + st * stage_bytes;
+            for (int w = 0; w < 2; ++w) {
+                for (int kk = 0; kk < ksteps; ++kk) {
+                    const uint32_t koff = (uint32_t)kk * 32u;
+                    ptx::mma_f16_ss_elect(tmem + (uint32_t)w * 128u,
+                                          ptx::smem_desc_at(hi_x, aXi + (uint32_t)w * xbytes + koff),
+                                          ptx::smem_desc_at(hi_x, aXj + koff), id_s, kk > 0 ? 1u : 0u);
                 }
+                ptx::mma_commit_elect(&bars.s_full[w]);
             }
-            // value product of tile tp: whole tile (single P) or K-block tk (hi + lo P)
-            if (tp < ts) {
-                const uint32_t g = gt + tp;
-                const uint32_t kb = PSPLIT ? tk : 0u;
+            if (t + 1 == T) ptx::mma_commit_elect(&bars.xi_empty[xb]);   // last use of the row tiles
+            if (++st == S) { st = 0; ph ^= 1u; }
+        }
+    }
+    ptx::mma_commit_elect(&bars.drain[0]);
+    warp_wait(&bars.drain[0], 0, p.limit_ns);
+    if (!ok && (threadIdx.x & 31) == 0) record_error(p.err, DEV_TIMEOUT);
+}
+
+// Value-product issuer: O^T += Vt_j P_j^T for each tile (single P: the whole
+// tile once both K-blocks are stored; hi + lo P: per K-block), then releases
+// the P buffer and the stage; O^T is handed to the epilogue after an item.
+template <int PSPLIT>
+__device__ void tp_mma_pv(const TpParams& p, TpBarriers& bars, const uint8_t* sSt, const uint8_t* sP,
+                          uint32_t xbytes, uint32_t vtbytes, uint32_t tmem, uint32_t id_pv) {
+    const uint32_t S = (uint32_t)p.stages;
+    const uint32_t aSt = ptx::smem_u32(sSt);
+    const uint32_t aP = ptx::smem_u32(sP);
+    const uint32_t stage_bytes = xbytes + vtbytes;
+    const uint32_t kblk = (uint32_t)p.rv * 128u;
+    const uint32_t hi_128 = ptx::smem_desc_hi(1024u, 2u);
+    uint32_t g = 0, st = 0, ph = 0;
+    int ic = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x, ++ic) {
+        int ip, sp, j0, j1;
+        item_range(p, item, ip, sp, j0, j1);
+        const uint32_t T = (uint32_t)(j1 - j0);
+        for (uint32_t t = 0; t < T && ok; ++t, ++g) {
+            if (t == 0 && ic > 0 && !warp_wait(&bars.o_empty, (ic - 1) & 1, p.limit_ns)) { ok = false; break; }
+            // Vt_j of this stage: landed before S of this tile was issued (already complete)
+            if (!warp_wait(&bars.full[st], ph, p.limit_ns)) { ok = false; break; }
+            for (uint32_t kb = 0; kb < (PSPLIT ? 2u : 1u); ++kb) {
                 const uint32_t buf = PSPLIT ? kb : (g & 1u);
                 const uint32_t par = PSPLIT ? (g & 1u) : ((g >> 1) & 1u);
-                const bool o_free = (tp > 0) || (kb > 0) || (ic == 0) || ptx::mbar_test(&bars.o_empty, (ic - 1) & 1);
-                if (o_free && ptx::mbar_test(&bars.p_full[buf], par)) {
-                    ptx::tc_fence_after();
-                    const uint32_t st = (n + tp) % S;
-                    const uint32_t aV = aSt + st * stage_bytes + xbytes + kb * kblk;
-                    const uint32_t aPb = aP + buf * 2u * kPKBlock;
-                    // single P: K-blocks 0, 1 of the tile (8 steps); hi + lo: hi then lo of K-block kb
+                if (!warp_wait(&bars.p_full[buf], par, p.limit_ns)) { ok = false; break; }
+                ptx::tc_fence_after();
+                const uint32_t aV = aSt + st * stage_bytes + xbytes + kb * kblk;
+                const uint32_t aPb = aP + buf * 2u * kPKBlock;
+                // single P: K-blocks 0, 1 of the tile (8 steps); hi + lo: hi then lo of K-block kb
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const uint32_t kk = (uint32_t)(q & 3) * 32u, hq = (uint32_t)(q >> 2);
-                        const uint32_t aVq = PSPLIT ? aV + kk : aV + hq * kblk + kk;
-                        const uint32_t aPq = aPb + hq * kPKBlock + kk;
-                        ptx::mma_f16_ss(tmem + kTmemO, ptx::smem_desc_at(hi_128, aVq), ptx::smem_desc_at(hi_128, aPq),
-                                        id_pv, (tp > 0 || kb > 0 || q > 0) ? 1u : 0u);
-                    }
-                    ptx::mma_commit(&bars.p_empty[buf]);      // this P buffer may be rewritten
-                    if (!PSPLIT || kb == 1) {
-                        ptx::mma_commit(&bars.empty[st]);     // X_j and Vt_j of this stage are consumed
-                        ++tp;
-                    }
-                    if (PSPLIT) tk = kb ^ 1u;
-                    progressed = true;
+                for (int q = 0; q < 8; ++q) {
+                    const uint32_t kk = (uint32_t)(q & 3) * 32u, hq = (uint32_t)(q >> 2);
+                    const uint32_t aVq = PSPLIT ? aV + kk : aV + hq * kblk + kk;
+                    const uint32_t aPq = aPb + hq * kPKBlock + kk;
+                    ptx::mma_f16_ss_elect(tmem + kTmemO, ptx::smem_desc_at(hi_128, aVq),
+                                          ptx::smem_desc_at(hi_128, aPq), id_pv,
+                                          (t > 0 || kb > 0 || q > 0) ? 1u : 0u);
                 }
+                ptx::mma_commit_elect(&bars.p_empty[buf]);      // this P buffer may be rewritten
             }
-            if (progressed) {
-                idle_since = clock64();
-            } else {
-                __nanosleep(64);
-                if (clock64() - idle_since > limit) {
-                    ok = false;
-                    break;
-                }
-            }
+            if (!ok) break;
+            ptx::mma_commit_elect(&bars.empty[st]);             // X_j and Vt_j of this stage are consumed
+            if (++st == S) { st = 0; ph ^= 1u; }
         }
         if (!ok) break;
-        ptx::mma_commit(&bars.o_full);
-        n += T;
-        gt += T;
+        ptx::mma_commit_elect(&bars.o_full);
     }
-    ptx::mma_commit(&bars.drain);
-    ptx::mbar_wait(&bars.drain, 0, p.limit_ns);
-    if (!ok) record_error(p.err, DEV_TIMEOUT);
+    ptx::mma_commit_elect(&bars.drain[1]);
+    warp_wait(&bars.drain[1], 0, p.limit_ns);
+    if (!ok && (threadIdx.x & 31) == 0) record_error(p.err, DEV_TIMEOUT);
 }
 
 template <int BF16>
@@ -307,7 +320,25 @@ __device__ __forceinline__ void tp_chunk(const uint32_t (&r)[32], int h, int row
     }
 }
 
-template <int KIND, int BF16, int PSPLIT>
+// Half-precision kernel evaluation (RBF, FP16): the S tile comes from the
+// MMA as FP16 (one rounding of the exp2 argument), is loaded packed in pairs,
+// and 2^s is evaluated for both halves of a register by one ex2.approx.f16x2,
+// whose output is already the packed FP16 P the value product reads: no
+// FP32 -> FP16 conversion, one SFU instruction per two kernel values.
+// 32 columns [32 h, 32 h + 32) of this thread's P row from 16 packed S
+// registers, stored as four 16-byte chunks.
+__device__ __forceinline__ void tp_chunk_h(const uint32_t* r, int h, uint32_t pkb, uint32_t nsw) {
+    uint32_t pk[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) pk[e] = ptx::ex2_h2(r[e]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t c = (uint32_t)((h & 1) * 4 + q);
+        st_shared_v4(pkb + ((c ^ nsw) << 4), pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+    }
+}
+
+template <int KIND, int BF16, int PSPLIT, int HS>
 __device__ void tp_epilogue(const TpParams& p, TpBarriers& bars, const uint8_t* sP, uint32_t tmem, int wg, int wq,
                             int lane) {
     const int tl = wg & 1, ch = wg >> 1;              // row tile of the pair, column half (= K-block)
@@ -327,38 +358,58 @@ __device__ void tp_epilogue(const TpParams& p, TpBarriers& bars, const uint8_t* 
         const int it = 2 * ip + tl;   // this warpgroup's row tile
         for (uint32_t t = 0; t < T; ++t) {
             const uint32_t g = gt + t;
-            if (!ptx::mbar_wait(&bars.s_full[tl], g & 1, p.limit_ns)) { ok = false; break; }
+            if (!__all_sync(0xffffffffu, ptx::mbar_wait(&bars.s_full[tl], g & 1, p.limit_ns))) { ok = false; break; }
             ptx::tc_fence_after();
             const uint32_t tS = tmem + lane_off + (uint32_t)tl * 128u + (uint32_t)ch * 64u;
             const bool dtile = (KIND == GP_KERNEL_MATERN12) && p.diag && (j0 + (int)t == it);
-            uint32_t ra[32], rb[32];
-            ptx::tmem_ld32(tS, ra);
-            ptx::tmem_ld32(tS + 32u, rb);
-            ptx::tmem_wait_ld();
-            ptx::tmem_reg_fence(ra);
-            ptx::tmem_reg_fence(rb);
+            uint32_t ra[32], rb[HS ? 1 : 32];
+            if constexpr (HS) {
+                ptx::tmem_ld32_pack16(tS, ra);     // 64 FP16 columns in 32 registers
+                ptx::tmem_wait_ld();
+                ptx::tmem_reg_fence(ra);
+            } else {
+                ptx::tmem_ld32(tS, ra);
+                ptx::tmem_ld32(tS + 32u, rb);
+                ptx::tmem_wait_ld();
+                ptx::tmem_reg_fence(ra);
+                ptx::tmem_reg_fence(rb);
+            }
             ptx::tc_fence_before();
-            ptx::mbar_arrive(&bars.s_empty[tl]);   // this half of S is in registers
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&bars.s_empty[tl]);   // this warp's part of S is in registers
             uint32_t buf;
             if constexpr (PSPLIT) {
                 // K-block buffer ch is free once the previous tile's product of it is done
                 buf = (uint32_t)ch;
-                if (g >= 1 && !ptx::mbar_wait(&bars.p_empty[buf], (g - 1) & 1, p.limit_ns)) { ok = false; break; }
+                if (g >= 1 && !__all_sync(0xffffffffu, ptx::mbar_wait(&bars.p_empty[buf], (g - 1) & 1, p.limit_ns))) {
+                    ok = false;
+                    break;
+                }
             } else {
                 // tile slot g & 1 is free once the product of tile g - 2 is done
                 buf = g & 1u;
-                if (g >= 2 && !ptx::mbar_wait(&bars.p_empty[buf], ((g >> 1) - 1) & 1, p.limit_ns)) { ok = false; break; }
+                if (g >= 2 &&
+                    !__all_sync(0xffffffffu, ptx::mbar_wait(&bars.p_empty[buf], ((g >> 1) - 1) & 1, p.limit_ns))) {
+                    ok = false;
+                    break;
+                }
             }
             const uint32_t pkb = aProw + buf * 2u * kPKBlock + (PSPLIT ? 0u : (uint32_t)ch * kPKBlock);
-            tp_chunk<KIND, BF16, PSPLIT>(ra, 2 * ch, row, dtile, pkb, nsw);
-            tp_chunk<KIND, BF16, PSPLIT>(rb, 2 * ch + 1, row, dtile, pkb, nsw);
+            if constexpr (HS) {
+                tp_chunk_h(ra, 2 * ch, pkb, nsw);
+                tp_chunk_h(ra + 16, 2 * ch + 1, pkb, nsw);
+            } else {
+                tp_chunk<KIND, BF16, PSPLIT>(ra, 2 * ch, row, dtile, pkb, nsw);
+                tp_chunk<KIND, BF16, PSPLIT>(rb, 2 * ch + 1, row, dtile, pkb, nsw);
+            }
             ptx::fence_proxy_async_smem();        // P stores -> visible to the tensor core
-            ptx::mbar_arrive(&bars.p_full[buf]);
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&bars.p_full[buf]);
         }
         if (!ok) break;
         if (!ok) break;
         // O^T read-out: lanes [0, rv) are the rows of Vt; this warpgroup's 64 columns.
-        if (!ptx::mbar_wait(&bars.o_full, ic & 1, p.limit_ns)) { ok = false; break; }
+        if (!__all_sync(0xffffffffu, ptx::mbar_wait(&bars.o_full, ic & 1, p.limit_ns))) { ok = false; break; }
         ptx::tc_fence_after();
         if (wq * 32 < p.rv) {   // warp-uniform
             const int r = wq * 32 + lane;
@@ -376,7 +427,8 @@ __device__ void tp_epilogue(const TpParams& p, TpBarriers& bars, const uint8_t* 
             }
         }
         ptx::tc_fence_before();
-        ptx::mbar_arrive(&bars.o_empty);
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&bars.o_empty);
         gt += T;
     }
     if (!ok) record_error(p.err, DEV_TIMEOUT);
@@ -408,7 +460,7 @@ __host__ __device__ inline TpSmem tp_smem(int k_pad, int rv, int psplit) {
     return m;
 }
 
-template <int KIND, int BF16, int PSPLIT>
+template <int KIND, int BF16, int PSPLIT, int HS>
 __global__ void __launch_bounds__(kThreads, 1)
 kmvm_tp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmV, const TpParams p) {
@@ -430,15 +482,16 @@ kmvm_tp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
         for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(&bars.s_full[b], 1);
-            ptx::mbar_init(&bars.s_empty[b], 256);              // the two warpgroups of a row tile
+            ptx::mbar_init(&bars.s_empty[b], 8);                // the 8 warps of a row tile (one arrival each)
             ptx::mbar_init(&bars.xi_full[b], 1);
             ptx::mbar_init(&bars.xi_empty[b], 1);
-            ptx::mbar_init(&bars.p_full[b], PSPLIT ? 256 : 512); // K-block: 2 warpgroups; tile: all 4
+            ptx::mbar_init(&bars.p_full[b], PSPLIT ? 8 : 16);   // K-block: 2 warpgroups; tile: all 4 (per warp)
             ptx::mbar_init(&bars.p_empty[b], 1);
         }
         ptx::mbar_init(&bars.o_full, 1);
-        ptx::mbar_init(&bars.o_empty, kEpiWarps * 32);
-        ptx::mbar_init(&bars.drain, 1);
+        ptx::mbar_init(&bars.o_empty, kEpiWarps);
+        ptx::mbar_init(&bars.drain[0], 1);
+        ptx::mbar_init(&bars.drain[1], 1);
         ptx::fence_mbar_init();
     }
     if (warp == kTmaWarp && lane == 0) {
@@ -456,12 +509,12 @@ kmvm_tp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         if (lane == 0) tp_producer(p, &tmA, &tmB, &tmV, bars, sSt, sXi, m.xbytes, m.vtbytes);
         __syncwarp();
     } else if (warp == kMmaWarp) {
-        if (lane == 0)
-            tp_mma<PSPLIT>(p, bars, sSt, sP, sXi, m.xbytes, m.vtbytes, tmem, ptx::idesc_f16(kBM, kBN, BF16),
-                   ptx::idesc_f16(kBM, kPairRows, BF16));
-        __syncwarp();
+        tp_mma_s(p, bars, sSt, sXi, m.xbytes, m.vtbytes, tmem,
+                 HS ? ptx::idesc_f16_dh(kBM, kBN) : ptx::idesc_f16(kBM, kBN, BF16));
+    } else if (warp == kPvWarp) {
+        tp_mma_pv<PSPLIT>(p, bars, sSt, sP, m.xbytes, m.vtbytes, tmem, ptx::idesc_f16(kBM, kPairRows, BF16));
     } else {
-        tp_epilogue<KIND, BF16, PSPLIT>(p, bars, sP, tmem, warp >> 2, warp & 3, lane);
+        tp_epilogue<KIND, BF16, PSPLIT, HS>(p, bars, sP, tmem, warp >> 2, warp & 3, lane);
     }
     ptx::tc_fence_before();
     __syncthreads();
@@ -469,11 +522,11 @@ kmvm_tp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     if (warp == kMmaWarp) ptx::tmem_dealloc(tmem, kTmemCols);
 }
 
-template <int KIND, int BF16, int PSPLIT>
+template <int KIND, int BF16, int PSPLIT, int HS = 0>
 cudaError_t launch_tp_typed(const TcPlan& plan, const TpParams& prm, const CUtensorMap& a, const CUtensorMap& b,
                             const CUtensorMap& v, cudaStream_t s) {
     const TpSmem m = tp_smem(prm.k_pad, prm.rv, PSPLIT);
-    auto kfn = kmvm_tp_kernel<KIND, BF16, PSPLIT>;
+    auto kfn = kmvm_tp_kernel<KIND, BF16, PSPLIT, HS>;
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m.total);
     if (e != cudaSuccess) return e;
     kfn<<<plan.grid, kThreads, m.total, s>>>(a, b, v, prm);
@@ -543,6 +596,8 @@ int launch_kmvm_tp(Ctx* ctx, const TcPlan& plan, const OperandLayout& L, const M
     prm.limit_ns = kWaitLimitNs;
     const int bf = (L.prec == GP_PREC_BF16) ? 1 : 0;
     cudaError_t e = cudaErrorInvalidValue;
+    const bool hs = L.half_exp != 0;
+    if (hs && !(a.kernel == GP_KERNEL_RBF && !bf && !L.psplit && plan.k_pad == 16)) return GP_ERR_UNSUPPORTED;
     prof_begin(ctx, s);
 #define GPK_TP_CASE(K)                                                                              \
     case K:                                                                                         \
@@ -553,7 +608,9 @@ int launch_kmvm_tp(Ctx* ctx, const TcPlan& plan, const OperandLayout& L, const M
             e = L.psplit ? launch_tp_typed<K, 0, 1>(plan, prm, tmA, tmB, tmV, s)                     \
                          : launch_tp_typed<K, 0, 0>(plan, prm, tmA, tmB, tmV, s);                    \
         break;
-    switch (a.kernel) {
+    if (hs) {
+        e = launch_tp_typed<GP_KERNEL_RBF, 0, 0, 1>(plan, prm, tmA, tmB, tmV, s);
+    } else switch (a.kernel) {
         GPK_TP_CASE(GP_KERNEL_RBF)
         GPK_TP_CASE(GP_KERNEL_MATERN32)
         GPK_TP_CASE(GP_KERNEL_MATERN12)

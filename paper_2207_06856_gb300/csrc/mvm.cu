@@ -70,6 +70,17 @@ static void kop_layout(A& a, KOp& op, int64_t Nr, int64_t Nc, int R_max, bool sq
     }
 }
 
+int check_mvm_flags(int flags, bool allow_noise) {
+    const int prec = flags & 0xff;
+    if (prec != GP_PREC_FP32 && prec != GP_PREC_FP16 && prec != GP_PREC_BF16) return GP_ERR_INVALID;
+    const int known = 0xff | GP_MVM_ADD_NOISE | GP_MVM_XSPLIT | GP_MVM_NO_XSPLIT | GP_MVM_SCALE_SQRT_N |
+                      GP_MVM_VSPLIT | GP_MVM_BF16_SINGLE | GP_MVM_ONE_TILE | GP_MVM_PSPLIT | GP_MVM_HALF_EXP;
+    if (flags & ~known) return GP_ERR_INVALID;
+    if (!allow_noise && (flags & GP_MVM_ADD_NOISE)) return GP_ERR_INVALID;
+    if ((flags & GP_MVM_XSPLIT) && (flags & GP_MVM_NO_XSPLIT)) return GP_ERR_INVALID;
+    return GP_OK;
+}
+
 static int kop_plan(const Ctx* ctx, KOp& op, const gp_hyp_t* hyp, int64_t Nr, int64_t Nc, int R, int flags) {
     op.kernel = hyp->kernel;
     op.d = hyp->d;
@@ -113,6 +124,10 @@ static int kop_plan(const Ctx* ctx, KOp& op, const gp_hyp_t* hyp, int64_t Nr, in
         }
         op.lay = make_layout(hyp->d, op.prec, xsplit, vsplit, psplit);
         if (op.lay.k_pad == 0) return GP_ERR_UNSUPPORTED;
+        if (flags & GP_MVM_HALF_EXP) {
+            if (bf || !pair || psplit || op.lay.k_pad != 16 || hyp->kernel != GP_KERNEL_RBF) return GP_ERR_UNSUPPORTED;
+            op.lay.half_exp = 1;
+        }
         op.tp = pair ? tp_plan(ctx, Nr, Nc, Rc, op.lay.k_pad, vsplit) : tc_plan(ctx, Nr, Nc, Rc, op.lay.k_pad);
     } else {
         return GP_ERR_INVALID;

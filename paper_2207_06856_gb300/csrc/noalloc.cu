@@ -49,12 +49,7 @@ int check_args(const gp_hyp_t* hyp, const float* Xr, int64_t Nr, const float* Xc
     GPK_TRY(gpk::check_hyp(hyp));
     if (Nr < 1 || Nc < 1 || Nr > (int64_t(1) << 31) - 256 || Nc > (int64_t(1) << 31) - 256) return GP_ERR_INVALID;
     if (R < 1 || R > 64) return GP_ERR_INVALID;
-    const int prec = flags & 0xff;
-    if (prec != GP_PREC_FP32 && prec != GP_PREC_FP16 && prec != GP_PREC_BF16) return GP_ERR_INVALID;
-    const int known = 0xff | GP_MVM_ADD_NOISE | GP_MVM_XSPLIT | GP_MVM_NO_XSPLIT | GP_MVM_SCALE_SQRT_N |
-                      GP_MVM_VSPLIT | GP_MVM_BF16_SINGLE;
-    if (flags & ~known) return GP_ERR_INVALID;
-    if ((flags & GP_MVM_XSPLIT) && (flags & GP_MVM_NO_XSPLIT)) return GP_ERR_INVALID;
+    GPK_TRY(gpk::check_mvm_flags(flags, true));   // the same flags as gp_kmvm
     if ((flags & GP_MVM_ADD_NOISE) && (Xr != Xc || Nr != Nc)) return GP_ERR_INVALID;
     const char* vb = (const char*)V;
     const char* ve = vb + (size_t)Nc * R * sizeof(float);

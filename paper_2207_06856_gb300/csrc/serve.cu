@@ -157,9 +157,8 @@ int check_opts(const gp_server_opts_t* o) {
     if (o->rank < 0 || o->rank > 512 || !(o->tol >= 0.0) || o->max_iter < 1 || o->max_iter > 1000) return GP_ERR_INVALID;
     if (o->restarts < 0 || o->restarts > 16) return GP_ERR_INVALID;
     if (o->reorth < GP_REORTH_NONE || o->reorth > GP_REORTH_EUCLID) return GP_ERR_INVALID;
-    const int p = o->precision & 0xff, mp = o->mean_precision & 0xff;
-    if (p < GP_PREC_FP32 || p > GP_PREC_BF16 || mp < GP_PREC_FP32 || mp > GP_PREC_BF16) return GP_ERR_INVALID;
-    if ((o->precision | o->mean_precision) & GP_MVM_ADD_NOISE) return GP_ERR_INVALID;
+    GPK_TRY(check_mvm_flags(o->precision, false));
+    GPK_TRY(check_mvm_flags(o->mean_precision, false));
     return GP_OK;
 }
 

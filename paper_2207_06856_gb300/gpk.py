@@ -46,6 +46,7 @@ MVM_VSPLIT = 0x1000
 MVM_BF16_SINGLE = 0x2000
 MVM_ONE_TILE = 0x4000
 MVM_PSPLIT = 0x8000
+MVM_HALF_EXP = 0x10000
 
 
 def _check_flags(check_precision, prec: int) -> int:

@@ -227,3 +227,80 @@ def test_kmvm_rejects_bad_arguments(ctx):
     with pytest.raises(gpk.GPKError):
         gpk.kmvm(ctx, gpk.Hyper(0, np.ones(3), 1.0, 0.1), X, torch.randn(65, 10, device=dev))
 
+
+
+HALF_SHAPES = [(1, 1, 1), (100, 3, 1), (129, 4, 16), (700, 8, 17), (1000, 11, 5), (2048, 8, 17), (4097, 2, 2),
+               (2048, 8, 64), (3001, 12, 9)]
+
+
+@pytest.mark.parametrize("shape", HALF_SHAPES)
+def test_kmvm_half_exp_matches_oracle(ctx, shape):
+    """Half-precision kernel evaluation (GP_MVM_HALF_EXP, RBF, FP16): the exp2
+    argument is rounded once to FP16 by the tensor core (11 significant bits,
+    round to nearest) and 2^s is evaluated in FP16.  Per value that adds a
+    relative error of at most 2^-11 |s| ln 2 for the argument and one FP16
+    ulp for the exponential; over a row sum these average like the FP16
+    rounding of the kernel value itself, so the 2e-3 bound of the FP16 MVM
+    holds."""
+    from paper_2207_06856_gb300 import gpk
+    N, d, R = shape
+    X, V, _, ls, a2, s2 = workloads.random_problem(N, d, R, seed=5 * N + d + R, kernel=0, lengthscale=1.0,
+                                                   outputscale=1.3, noise=0.05)
+    got = _run(ctx, X, V, 0, ls, a2, s2, "fp16", flags=gpk.MVM_HALF_EXP)
+    assert _colerr(got, _ref(X, V, 0, ls, a2, s2)) <= TOL["fp16"]
+
+
+def test_kmvm_half_exp_limits(ctx):
+    """Rank-one (l -> infinity: every argument rounds to 0, 2^0 = 1 exactly) and
+    far-apart (arguments below -2^4: the FP16 exponential underflows to 0)
+    limits of the half-precision evaluation."""
+    from paper_2207_06856_gb300 import gpk
+    X, V, _, _, _, _ = workloads.random_problem(900, 5, 4, seed=7)
+    V = V + 1.0
+    got = _run(ctx, X, V, 0, np.full(5, 1e6, np.float32), 1.7, 0.1, "fp16", flags=gpk.MVM_HALF_EXP)
+    ref = 1.7 * np.ones((4, 900)) * V.astype(np.float64).sum(axis=1, keepdims=True) + 0.1 * V
+    assert _colerr(got, ref) <= TOL["fp16"]
+    g = np.arange(8, dtype=np.float32)
+    Xg = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3) + 100.0
+    Vg = np.random.default_rng(8).standard_normal((3, Xg.shape[0])).astype(np.float32)
+    got = _run(ctx, Xg, Vg, 0, np.full(3, 0.1, np.float32), 0.9, 0.2, "fp16", flags=gpk.MVM_HALF_EXP)
+    assert _colerr(got, 1.1 * Vg.astype(np.float64)) <= TOL["fp16"]
+
+
+def test_kmvm_half_exp_precision_workload_sampled_rows(ctx):
+    """The benchmark's MVM shape with the half-precision evaluation: 256
+    sampled rows against exact FP64 rows."""
+    from paper_2207_06856_gb300 import gpk
+    w = workloads.precision()
+    dev = torch.device("cuda:0")
+    B = w.rhs()
+    hyp = gpk.Hyper(w.kernel, w.lengthscale, w.outputscale, w.noise)
+    out = gpk.kmvm(ctx, hyp, torch.from_numpy(w.X).to(dev), torch.from_numpy(B).to(dev), precision="fp16",
+                   add_noise=True, flags=gpk.MVM_HALF_EXP)
+    ctx.check()
+    got = out.cpu().numpy().astype(np.float64)
+    rows = np.sort(np.random.default_rng(11).choice(w.N, 256, replace=False))
+    ref = O.kmvm_rows(w.X, rows, B.T.astype(np.float64), O.Hyp("rbf", w.lengthscale, w.outputscale, w.noise)).T
+    assert _colerr(got[:, rows], ref) <= TOL["fp16"]
+
+
+@pytest.mark.parametrize("case", ["matern32", "bf16", "d18", "psplit", "one_tile"])
+def test_kmvm_half_exp_unsupported(ctx, case):
+    """The half-precision evaluation exists for RBF, FP16, a contraction width
+    of 16 and the pair engine with a single-term tile; anything else is
+    refused (GP_ERR_UNSUPPORTED), never silently run another way."""
+    from paper_2207_06856_gb300 import gpk
+    kern, prec, d, fl = 0, "fp16", 8, gpk.MVM_HALF_EXP
+    if case == "matern32":
+        kern = 1
+    elif case == "bf16":
+        prec = "bf16"
+    elif case == "d18":
+        d = 18
+    elif case == "psplit":
+        fl |= gpk.MVM_PSPLIT
+    else:
+        fl |= gpk.MVM_ONE_TILE
+    X, V, _, ls, a2, s2 = workloads.random_problem(300, d, 3, seed=2, kernel=kern)
+    with pytest.raises(gpk.GPKError):
+        _run(ctx, X, V, kern, ls, a2, s2, prec, flags=fl)
