@@ -166,34 +166,35 @@ def test_cg_edge_cases(ctx):
     ctx.check()
 
 
+STOP_MARGIN = 0.01   # the benchmark's margin under 1e-2 for the FP32 check's rounding
+
+
 def test_precision_workload_full_size_fp16(ctx):
     """The benchmark solve: N = 65,536, d = 8, RBF, 1 + 16 RHS, rank-100
-    preconditioner, FP16 tensor-core MVM, stable CG to 1e-2.
+    preconditioner, FP16 tensor-core MVM, stable CG stopped at 0.99e-2 on its
+    FP32 true-residual check.
 
-    The solver's final relative residual comes from its FP32 true-residual MVM
-    over all N rows (rounding ~1e-6 of ||b||, far below the tolerance) and must
-    be <= 1e-2.  It is recomputed in FP64 on 4096 sampled rows as the unbiased
-    estimate sqrt(N/n sum_S r_i^2) / ||b||; with n = 4096 its relative sampling
-    error is ~1.5 %, so the estimate must agree with the reported value to 10 %
-    and stay below 1.1e-2."""
+    The residual ||Ktilde U - B|| / ||B|| is recomputed in FP64 over all
+    65,536 rows (the oracle's multi-threaded matrix-free MVM) and must be
+    <= 1e-2 for every column: the 1 % margin covers the FP32 check's rounding,
+    about 2^-24 kappa / sqrt(N) = 3.4e-6 of ||b|| with kappa = || |K| |x| || /
+    ||b|| ~ 1.5e4 (sum_j |k_ij x_j| rather than |(Ktilde x)_i| sets it)."""
+    from oracle import cfp64 as C
     from paper_2207_06856_gb300 import gpk
     w = workloads.precision()
     hyp = gpk.Hyper(w.kernel, w.lengthscale, w.outputscale, w.noise)
     X = _dev(w.X)
     pc = gpk.pivchol(ctx, hyp, X, w.rank)
     B = w.rhs()
-    U, st, info = gpk.cg_solve(ctx, hyp, X, _dev(B), pc, tol=w.tol, max_iter=w.max_iter, precision="fp16")
+    U, st, info = gpk.cg_solve(ctx, hyp, X, _dev(B), pc, tol=w.tol * (1.0 - STOP_MARGIN), max_iter=w.max_iter,
+                               precision="fp16")
     ctx.check()
     assert st == gpk.GP_OK, (info["col_iters"], info["rel_resid"])
     reported = np.asarray(info["rel_resid"])
-    assert reported.max() <= w.tol, reported
-    n = 4096
-    rows = np.sort(np.random.default_rng(25).choice(w.N, n, replace=False))
-    Bt = B.T.astype(np.float64)
-    r = O.kmvm_rows(w.X, rows, U.cpu().numpy().T, _ohyp(w), add_noise=True) - Bt[rows]
-    est = np.sqrt(w.N / n * np.sum(r * r, axis=0)) / np.linalg.norm(Bt, axis=0)
-    assert est.max() <= 1.1 * w.tol, est
-    assert np.all(np.abs(est / reported - 1.0) <= 0.10), (est, reported)
+    assert reported.max() <= w.tol * (1.0 - STOP_MARGIN), reported
+    full = C.relative_residual(w.X, U.cpu().numpy().T, B.T, _ohyp(w))
+    assert full.max() <= w.tol, full
+    assert np.all(np.abs(full - reported) <= STOP_MARGIN * w.tol), (full, reported)
 
 
 def test_breakdown_escalates_to_check_precision(ctx):
