@@ -183,11 +183,20 @@ GPK_API int gp_kmvm(gp_ctx* ctx, const gp_hyp_t* hyp,
  * - Every call shares the array: calls whose work overlaps on the GPU (for
  *   example on two unordered streams) race and corrupt each other.
  * - Asynchronous on `stream` like gp_kmvm; a device-side wait that runs out
- *   is recorded in the shared array, not reported by this call.
+ *   (or another device-side status) is recorded in an error word at the
+ *   start of the shared array: read it with gp_kmvm_noalloc_check.
+ * - The array's device address is cached per device for the life of the
+ *   process; it does not survive a reset of the device's primary context
+ *   (cudaDeviceReset): make no call after one.
  * The paper has no counterpart: this is a deployment variant of Eq. mvm. */
 #define GPK_NOALLOC_SCRATCH_BYTES (16u << 20)
 GPK_API int gp_kmvm_noalloc(const gp_hyp_t* hyp, const float* Xr, int64_t Nr, const float* Xc, int64_t Nc,
                             const float* V, int R, float* out, int flags, void* stream);
+/* Status of the gp_kmvm_noalloc calls on the current device since the last
+ * check: synchronises `stream`, reads the error word of the shared array and
+ * clears it.  Returns GP_OK, GP_ERR_TIMEOUT (a bounded device-side wait ran
+ * out), GP_ERR_NONFINITE, or GP_ERR_CUDA.  Allocates nothing. */
+GPK_API int gp_kmvm_noalloc_check(void* stream);
 
 /* ---- S3: pivoted-Cholesky preconditioner (Sec. 4.2, Eq. woodbury) ---------
  * k = rank steps of partial pivoted Cholesky of K (no noise) from kernel rows

@@ -89,3 +89,21 @@ extern "C" int gp_kmvm_noalloc(const gp_hyp_t* hyp, const float* Xr, int64_t Nr,
     GPK_TRY(gpk::kop_prepare(&c, wc, op, hyp, Xr, Nr, Xc, Nc, R, mvm_flags, s));
     return gpk::kop_apply(&c, op, V, R, out, Nr, (flags & GP_MVM_ADD_NOISE) != 0, s);
 }
+
+extern "C" int gp_kmvm_noalloc_check(void* stream) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GP_ERR_CUDA;
+    void* base = nullptr;
+    GPK_TRY(scratch_address(dev, &base));
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return GP_ERR_CUDA;
+    int v = 0;
+    if (cudaMemcpy(&v, base, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return GP_ERR_CUDA;
+    if (v == gpk::DEV_OK) return GP_OK;
+    if (cudaMemset(base, 0, sizeof(int)) != cudaSuccess) return GP_ERR_CUDA;
+    switch (v) {
+        case gpk::DEV_TIMEOUT: return GP_ERR_TIMEOUT;
+        case gpk::DEV_NONFINITE: return GP_ERR_NONFINITE;
+        case gpk::DEV_BREAKDOWN: return GP_ERR_BREAKDOWN;
+    }
+    return GP_ERR_CUDA;
+}

@@ -426,6 +426,15 @@ def kmvm_noalloc(hyp: Hyper, Xr, V, Xc=None, precision="fp16", add_noise=False, 
     return out
 
 
+def kmvm_noalloc_status(stream=None) -> int:
+    """gp_kmvm_noalloc_check: device-side status of the no-alloc calls on the
+    current device since the last check (synchronises the stream, clears it)."""
+    fn = lib().gp_kmvm_noalloc_check
+    fn.restype = _c_int
+    fn.argtypes = [_c_void_p]
+    return int(fn(_stream_ptr(stream)))
+
+
 MLL_PRECOND_PROBES = 0x1
 MLL_WANT_LOGDET = 0x2
 
