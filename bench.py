@@ -56,7 +56,7 @@ STOP_MARGIN = 0.01
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one kmvm_tp_kernel launch,
 # keyed by the launch it was captured on (kernel, precision, N, R, flags); the
 # roofline reports it only for that exact launch and null otherwise.
-KMVM_TRAFFIC_BYTES = {}
+KMVM_TRAFFIC_BYTES = {("rbf", "fp16", 65536, 17, 0): 12.793088e6 + 12.288256e6}
 
 
 def _peaks_file():
@@ -349,6 +349,25 @@ def run_ours(args):
                          + ("" if converged else f", extrapolated to {iters} iterations ({FP32_ITERS_NOTE})"),
                "extrapolated": not converged, "iters_timed": it_done, "s_per_iter": t_iter}
 
+    # --- the other workloads on the same GPU, reduced counts (rank 0, N = 1 only) -----
+    extras = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        extras = {}
+        t0 = time.perf_counter()
+        d = diff_measure(args, args.extra_diff_steps)
+        extras["differentiation"] = {k: d[k] for k in ("value", "unit", "steps", "config", "loss_first", "loss_last",
+                                                       "subsample_exact_nll_initial", "subsample_exact_nll_final",
+                                                       "cg_iters", "clocks")}
+        sc = scale_measure(args)
+        extras["scale"] = {k: sc[k] for k in ("value", "unit", "config", "mll", "cg_iters", "rel_resid_y_reported",
+                                              "rel_resid_y_fp64_sampled_512_rows", "pairs_per_mvm", "clocks")}
+        sv = serve_measure(args, args.extra_serve_requests, n_calib=32)
+        extras["serving"] = {k: sv[k] for k in ("p50_ms", "p99_ms", "mean_ms", "solves_per_s",
+                                                "saturated_solves_per_s", "offered_rate_per_s", "all_ok",
+                                                "rel_resid_max", "max_inflight", "config", "clocks")}
+        extras["serving"]["requests"] = args.extra_serve_requests
+        extras["wall_s"] = time.perf_counter() - t0
+
     if rank == 0:
         inf = infos[-1]
         line = {
@@ -374,6 +393,12 @@ def run_ours(args):
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": gpu_launches,
             "clocks": clocks,
+            "adam_step_s": None if extras is None else extras["differentiation"]["value"],
+            "scale_mll_grad_step_s": None if extras is None else extras["scale"]["value"],
+            "serve_p50_ms": None if extras is None else extras["serving"]["p50_ms"],
+            "serve_p99_ms": None if extras is None else extras["serving"]["p99_ms"],
+            "serve_solves_per_s": None if extras is None else extras["serving"]["solves_per_s"],
+            "other_workloads": extras,
             "peaks_file": {k: _peaks_file().get(k) for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained")},
         }
         print(json.dumps(line), flush=True)
@@ -419,6 +444,10 @@ def run_kmvm(args):
 
 
 def run_serve(args):
+    print(json.dumps(serve_measure(args, args.serve_requests)), flush=True)
+
+
+def serve_measure(args, n_requests, n_calib=None):
     """Serving workload: 512 posterior-mean requests (N log-uniform in [1k, 200k],
     d in {4, 8, 16}, RBF / Matern-3/2, 1024 test points each), FP16 MVM + CG to
     1e-2 with a rank-20 preconditioner.  First the saturated throughput is
@@ -428,7 +457,7 @@ def run_serve(args):
     import torch
     from paper_2207_06856_gb300 import gpk, workloads
     torch.cuda.set_device(0)
-    reqs = workloads.serving(n_requests=args.serve_requests, rate_per_s=1.0, seed=1)
+    reqs = workloads.serving(n_requests=512, rate_per_s=1.0, seed=1)[:n_requests]
     pin = gpk.Server.pinned
     inputs = [(gpk.Hyper(r.kernel, r.lengthscale, r.outputscale, r.noise), pin(r.X), pin(r.y), pin(r.Xstar))
               for r in reqs]
@@ -439,7 +468,8 @@ def run_serve(args):
     for r in small:   # warm-up
         srv.submit(gpk.Hyper(r.kernel, r.lengthscale, r.outputscale, r.noise), r.X, r.y, r.Xstar).result()
     # saturated throughput: a random subset submitted at once
-    cal = np.random.default_rng(3).choice(len(inputs), min(args.serve_calib, len(inputs)), replace=False)
+    n_calib = args.serve_calib if n_calib is None else n_calib
+    cal = np.random.default_rng(3).choice(len(inputs), min(n_calib, len(inputs)), replace=False)
     t0 = time.perf_counter()
     futs = [srv.submit(*inputs[i]) for i in cal]
     for f in futs:
@@ -479,7 +509,8 @@ def run_serve(args):
         "metric": "serve_latency_p99", "value": float(np.percentile(lat, 99)), "unit": "ms", "n_gpus": 1,
         "steps": len(reqs), "warmup": len(small), "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "fp16", "data": "synthetic",
-        "config": {"workload": f"serving: {len(reqs)} posterior-mean requests, Poisson arrivals at "
+        "config": {"workload": f"serving: {len(reqs)} posterior-mean requests (the first {len(reqs)} of the 512-request "
+                               f"trace), Poisson arrivals at "
                                f"{args.serve_load:.2f}x saturated rate, N log-uniform [1k, 200k], d in {{4,8,16}}, "
                                "RBF/Matern-3/2, 1024 test points, FP16 tensor-core MVM (kernel tile and inputs "
                                "as hi + lo) + stable CG to 1e-2, rank 20",
@@ -492,10 +523,14 @@ def run_serve(args):
         "oracle_mean_relerr_smallest3": check, "gpu_launches": int(st["launches"] - launches0),
         "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_diff(args):
+    print(json.dumps(diff_measure(args, args.diff_steps)), flush=True)
+
+
+def diff_measure(args, n_steps):
     """Differentiation workload: N = 262,144, d = 18 (ARD RBF, Gaussian-mixture
     inputs, random-feature targets), the training loop of the paper: Adam on the
     hyperparameters, each step one MLL + gradient (CG to 1.0 with 10 iterations
@@ -522,7 +557,7 @@ def run_diff(args):
     sampler.start()
     torch.cuda.synchronize()
     t_last[0] = time.perf_counter()
-    hist = autograd.fit(ctx, X, y, w.kernel, w.lengthscale, w.outputscale, w.noise, steps=args.diff_steps, lr=0.05,
+    hist = autograd.fit(ctx, X, y, w.kernel, w.lengthscale, w.outputscale, w.noise, steps=n_steps, lr=0.05,
                         M=16, rank=w.rank, tol=args.diff_tol, max_iter=args.diff_max_iter, min_iter=10,
                         precision=args.precision, callback=cb)
     clocks = sampler.stop()
@@ -550,10 +585,15 @@ def run_diff(args):
         "noise_last": hist[-1][3], "cg_iters": iters, "total_s": float(np.sum(step_s)),
         "gpu_launches": int(ctx.launches - launches0), "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
+    ctx.close()
+    return line
 
 
 def run_scale(args):
+    print(json.dumps(scale_measure(args)), flush=True)
+
+
+def scale_measure(args):
     """Scale workload: N = 1,843,200, d = 11, Matern-3/2 ARD: one full MLL +
     gradient step (rank-100 pivoted Cholesky, 1 + 16 right-hand sides with
     P-distributed probes, CG to 1.0 with 10..50 iterations, SLQ log-det, FP16
@@ -588,10 +628,11 @@ def run_scale(args):
     t = e0.elapsed_time(e1) / 1e3
     # sampled FP64 check of the y-solve: residual of column 0 on 512 rows
     import oracle as O
+    from oracle import cfp64 as C
     rows = np.sort(np.random.default_rng(3).choice(N, 512, replace=False))
     oh = O.Hyp(workloads.KERNEL_NAMES[w.kernel], w.lengthscale, w.outputscale, w.noise)
     u0 = U[0].cpu().numpy().astype(np.float64)
-    r = O.kmvm_rows(w.X, rows, u0[:, None], oh)[:, 0] - w.y[rows].astype(np.float64)
+    r = C.kmvm(w.X, u0[:, None], oh, rows=rows)[:, 0] - w.y[rows].astype(np.float64)
     est = float(np.sqrt(N / len(rows) * np.sum(r * r)) / np.linalg.norm(w.y.astype(np.float64)))
     line = {
         "metric": "mll_gradient_step_time", "value": t, "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0,
@@ -604,7 +645,8 @@ def run_scale(args):
         "rel_resid_y_reported": float(info["rel_resid"][0]), "rel_resid_y_fp64_sampled_512_rows": est,
         "pairs_per_mvm": float(N) * float(N), "gpu_launches": int(ctx.launches - launches0), "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
+    ctx.close()
+    return line
 
 
 def main():
@@ -621,6 +663,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--stop-margin", type=float, default=STOP_MARGIN)
     ap.add_argument("--measure-kappa", action="store_true", help="also report the cancellation factor")
+    ap.add_argument("--no-extras", action="store_true", help="skip the differentiation / scale / serving runs")
+    ap.add_argument("--extra-diff-steps", type=int, default=4)
+    ap.add_argument("--extra-serve-requests", type=int, default=96)
     ap.add_argument("--ref-iters", type=int, default=152)
     ap.add_argument("--mode", default="solve", choices=["solve", "kmvm", "serve", "diff", "scale"])
     ap.add_argument("--diff-steps", type=int, default=20)

@@ -327,6 +327,13 @@ GPK_API int gp_slq_quadrature(const double* alpha, const double* beta, int J, do
                                       with log|P| added exactly                       */
 #define GP_MLL_WANT_LOGDET    0x2  /* estimate log|Ktilde| by SLQ for the loss value
                                       (needs PRECOND_PROBES, or no preconditioner)     */
+/* Lanczos depth of the loss value, decoupled from the solve tolerance: with
+ * GP_MLL_WANT_LOGDET every column runs at least n (<= 255) CG iterations, so
+ * that the SLQ quadrature of each probe and y^T u_0 are taken from at least
+ * n Lanczos steps even at a loose training tolerance (such as 1.0, where the
+ * solve would otherwise stop at the iteration floor and the printed loss is
+ * not an estimate of the loss).  OR it into `flags`. */
+#define GP_MLL_SLQ_MIN_ITER(n) ((((int)(n)) & 0xff) << 8)
 /* Solves Ktilde [u_0 .. u_M] = [y, z_1 .. z_M] with gp_cg_solve's method, then
  *   grad[0..d+2) = gradient of 1/(2M) sum_j u_j^T (dKtilde w_j) - 1/2 u_0^T (dKtilde u_0)
  *                  w.r.t. (l_1..l_d, a^2, sigma^2)  (Eq. approx; host),

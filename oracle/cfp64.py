@@ -54,6 +54,8 @@ def _load():
         lib.orc_kmvm.restype = i32
         lib.orc_pcg.argtypes = [P, i64, i32, P, i32, f64, f64, P, i32, P, i32, P, f64, i32, f64, P, P, P, P]
         lib.orc_pcg.restype = i32
+        lib.orc_quad_form_grad.argtypes = [P, i64, i32, P, i32, f64, P, P, i32, P, P]
+        lib.orc_quad_form_grad.restype = i32
         lib.orc_threads.argtypes = []
         lib.orc_threads.restype = i32
         _lib = lib
@@ -133,6 +135,36 @@ def pcg(X, B, hyp: Hyp, L=None, tol: float = 1e-2, max_iter: int = 1000, time_li
     if rc != 0:
         raise RuntimeError(f"orc_pcg failed ({rc})")
     return U, int(it.value), rel, float(spi.value)
+
+
+def quad_form_grad(X, hyp: Hyp, U, V, wrt_X: bool = False):
+    """Gradient of q = sum_c u_c^T Ktilde v_c (u, v fixed) w.r.t. (l_1..l_d, a^2,
+    sigma^2) and optionally X: the same quantity as gp_oracle.quad_form_grad,
+    matrix-free on all host cores.  U, V: N x R.  Returns (g [d+2], gX or None)."""
+    X = _f64(X)
+    N, d = X.shape
+    U = _f64(np.asarray(U, dtype=np.float64).reshape(N, -1))
+    V = _f64(np.asarray(V, dtype=np.float64).reshape(N, -1))
+    ls = _f64(np.broadcast_to(hyp.lengthscale, (d,)))
+    g = np.empty(d + 2)
+    gX = np.empty((N, d)) if wrt_X else None
+    rc = _load().orc_quad_form_grad(_ptr(X), N, d, _ptr(ls), KERNEL_IDS[hyp.kernel], float(hyp.outputscale),
+                                    _ptr(U), _ptr(V), U.shape[1], _ptr(g), None if gX is None else _ptr(gX))
+    if rc != 0:
+        raise RuntimeError(f"orc_quad_form_grad failed ({rc})")
+    return g, gX
+
+
+def pseudo_loss_grad(X, hyp: Hyp, U, Z, W=None) -> np.ndarray:
+    """Eq. approx as in gp_oracle.pseudo_loss_grad, with the bilinear-form
+    gradients taken matrix-free (large N)."""
+    U = np.asarray(U, dtype=np.float64)
+    Z = np.asarray(Z, dtype=np.float64)
+    M = Z.shape[1]
+    Wp = Z if W is None else np.asarray(W, dtype=np.float64)
+    g_probe, _ = quad_form_grad(X, hyp, U[:, 1:], Wp)
+    g_y, _ = quad_form_grad(X, hyp, U[:, :1], U[:, :1])
+    return g_probe / (2.0 * M) - 0.5 * g_y
 
 
 def preconditioner(X, hyp: Hyp, rank: int):

@@ -40,6 +40,20 @@ static double unit_kernel(double r2, int kernel) {
     return (1.0 + s + s * s / 3.0) * exp(-s);
 }
 
+/* dk/d(r^2): the derivative every hyperparameter gradient uses.
+ * RBF -k/2; Matern-3/2 -(3/2) exp(-sqrt3 r); Matern-1/2 -exp(-r)/(2r), taken as
+ * 0 at r = 0 where the (x_i - x_j) factors it multiplies vanish; Matern-5/2
+ * -(5/6)(1 + sqrt5 r) exp(-sqrt5 r). */
+static double unit_kernel_dr2(double r2, int kernel) {
+    if (r2 < 0.0) r2 = 0.0;
+    if (kernel == 0) return -0.5 * exp(-0.5 * r2);
+    const double r = sqrt(r2);
+    if (kernel == 1) return -1.5 * exp(-sqrt(3.0) * r);
+    if (kernel == 2) return r > 0.0 ? -exp(-r) / (2.0 * r) : 0.0;
+    const double s = sqrt(5.0) * r;
+    return -(5.0 / 6.0) * (1.0 + s) * exp(-s);
+}
+
 int orc_threads(void) { return omp_get_max_threads(); }
 
 /* out[t] = (Ktilde V)[rows[t]] for t < nrows (rows == NULL: every row, nrows = N).
@@ -222,4 +236,65 @@ int orc_pcg(const double* X, int64_t N, int d, const double* ls, int kernel, dou
     *sec_per_iter = it > 0 ? (t1 - t0) / it : 0.0;
     free(r); free(z); free(dd); free(Kd);
     return rc;
+}
+
+/* Gradient of q = sum_c u_c^T Ktilde w_c with u, w held fixed (the quantity a
+ * backward pass through Eq. mvm returns), G_ij = sum_c u_ic w_jc:
+ *   g[m]   = dq/dl_m  = sum_ij G_ij a^2 k'(r^2_ij) (-2 (x_im - x_jm)^2 / l_m^3)
+ *   g[d]   = dq/da^2  = sum_ij G_ij k(r^2_ij)
+ *   g[d+1] = dq/dsigma^2 = sum_c u_c^T w_c
+ *   gX[i][m] (optional) = sum_j (G_ij + G_ji) a^2 k'(r^2_ij) 2 (x_im - x_jm) / l_m^2.
+ * U, W: N x R row-major; g: d + 2 doubles; gX: N x d row-major or NULL. */
+int orc_quad_form_grad(const double* X, int64_t N, int d, const double* ls, int kernel, double a2,
+                       const double* U, const double* W, int R, double* g, double* gX) {
+    if (!X || !ls || !U || !W || !g || N <= 0 || d <= 0 || d > 128 || R <= 0 || kernel < 0 || kernel > 3) return -1;
+    for (int m = 0; m < d + 2; ++m) g[m] = 0.0;
+    int bad = 0;
+#pragma omp parallel
+    {
+        double* acc = (double*)calloc((size_t)d + 2, sizeof(double));
+        double diff[128], gxi[128];
+        if (!acc) {
+#pragma omp atomic write
+            bad = 1;
+        }
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t i = 0; i < N; ++i) {
+            if (!acc) continue;
+            const double* xi = X + i * d;
+            for (int m = 0; m < d; ++m) gxi[m] = 0.0;
+            double uw = 0.0;
+            for (int c = 0; c < R; ++c) uw += U[i * R + c] * W[i * R + c];
+            acc[d + 1] += uw;
+            for (int64_t j = 0; j < N; ++j) {
+                const double* xj = X + j * d;
+                double r2 = 0.0;
+                for (int m = 0; m < d; ++m) {
+                    diff[m] = xi[m] - xj[m];
+                    const double t = diff[m] / ls[m];
+                    r2 += t * t;
+                }
+                double gij = 0.0, gji = 0.0;
+                for (int c = 0; c < R; ++c) {
+                    gij += U[i * R + c] * W[j * R + c];
+                    gji += U[j * R + c] * W[i * R + c];
+                }
+                const double k = unit_kernel(r2, kernel);
+                const double wk = a2 * unit_kernel_dr2(r2, kernel);
+                acc[d] += gij * k;
+                for (int m = 0; m < d; ++m) {
+                    acc[m] += gij * wk * (-2.0 * diff[m] * diff[m] / (ls[m] * ls[m] * ls[m]));
+                    gxi[m] += (gij + gji) * wk * 2.0 * diff[m] / (ls[m] * ls[m]);
+                }
+            }
+            if (gX)
+                for (int m = 0; m < d; ++m) gX[i * d + m] = gxi[m];
+        }
+        if (acc) {
+#pragma omp critical
+            for (int m = 0; m < d + 2; ++m) g[m] += acc[m];
+            free(acc);
+        }
+    }
+    return bad ? -2 : 0;
 }

@@ -47,7 +47,7 @@ __all__ = [
     "mll_grad_exact", "quad_form_grad", "pseudo_loss_grad",
     "lse_dot", "LSEBreakdown",
     "pivoted_cholesky", "woodbury_core", "precond_apply", "precond_logdet",
-    "cg_standard", "cg_stable", "CGResult",
+    "cg_standard", "cg_stable", "cg_mbcg", "CGResult",
     "lanczos_tridiagonal", "slq_quadrature",
     "max_distance", "relative_residual",
 ]
@@ -524,6 +524,51 @@ def cg_stable(matvec, b, x0=None, precond=None, tol=1e-6, max_iter=None,
         res.betas.append(beta)
         res.resid.append(float(np.linalg.norm(r)) / bnorm)
     res.x, res.iters = x, k
+    return res
+
+
+def cg_mbcg(matmat, B, precond=None, tol=1e-6, max_iter=None) -> list:
+    """mBCG (App. A): Alg. 1 on every column of B (N x R) at once.  Each column
+    keeps its own alpha_k, beta_k, gamma_k and stops on its own tolerance; the
+    only thing shared is that one matrix product K [d_1 .. d_R] serves all
+    columns per step.  Returns one CGResult per column (alphas, betas and
+    gamma0 feed lanczos_tridiagonal / slq_quadrature)."""
+    B = np.asarray(B, dtype=np.float64)
+    P = precond or _identity
+    N, R = B.shape
+    max_iter = N if max_iter is None else max_iter
+    X = np.zeros((N, R))
+    Rm = -B.copy()                       # r_0 = K x_0 - b with x_0 = 0
+    Z = P(Rm)
+    D = -Z
+    gamma = np.sum(Rm * Z, axis=0)
+    bnorm = np.linalg.norm(B, axis=0)
+    res = [CGResult(x=X[:, c], iters=0, gamma0=float(gamma[c])) for c in range(R)]
+    rel = np.linalg.norm(Rm, axis=0) / bnorm
+    for c in range(R):
+        res[c].resid.append(float(rel[c]))
+    active = rel > tol
+    k = 0
+    while np.any(active) and k < max_iter:
+        KD = matmat(D)
+        alpha = np.where(active, gamma / np.where(active, np.sum(D * KD, axis=0), 1.0), 0.0)
+        X = X + alpha * D
+        Rm = Rm + alpha * KD
+        Z = P(Rm)
+        gamma_new = np.sum(Rm * Z, axis=0)
+        beta = np.where(active, gamma_new / np.where(active, gamma, 1.0), 0.0)
+        D = np.where(active, -Z + beta * D, D)
+        gamma = np.where(active, gamma_new, gamma)
+        rel = np.linalg.norm(Rm, axis=0) / bnorm
+        k += 1
+        for c in np.nonzero(active)[0]:
+            res[c].alphas.append(float(alpha[c]))
+            res[c].betas.append(float(beta[c]))
+            res[c].resid.append(float(rel[c]))
+            res[c].iters = k
+        active = active & (rel > tol)
+    for c in range(R):
+        res[c].x = X[:, c]
     return res
 
 

@@ -34,7 +34,7 @@ class MarginalLikelihood(torch.autograd.Function):
         mll, g, gX, _, info = gpk.mll_and_grad(
             cfg.ctx, hyp, X, y, Z, precond=pc, E=E if cfg.precond_probes else None,
             precond_probes=cfg.precond_probes, want_logdet=cfg.want_logdet, tol=cfg.tol, max_iter=cfg.max_iter,
-            min_iter=cfg.min_iter, precision=cfg.precision, want_X=X.requires_grad)
+            min_iter=cfg.min_iter, precision=cfg.precision, want_X=X.requires_grad, loss_depth=cfg.loss_depth)
         cfg.last_info = info
         d = hyp.d
         fctx.grads = (torch.tensor(g[:d], dtype=lengthscale.dtype, device=lengthscale.device),
@@ -60,6 +60,7 @@ class FitConfig:
     precision: object = "fp16"
     precond_probes: bool = True
     want_logdet: bool = True
+    loss_depth: int = 0
     last_info: dict | None = None
 
 
@@ -69,7 +70,8 @@ def softplus_inv(x: float) -> float:
 
 def fit(ctx, X, y, kernel: int, init_lengthscale, init_outputscale: float, init_noise: float, steps: int = 20,
         lr: float = 0.05, M: int = 16, rank: int = 100, tol: float = 1.0, max_iter: int = 50,
-        precision="fp16", seed: int = 0, min_noise: float = 1e-4, callback=None, min_iter: int = 10):
+        precision="fp16", seed: int = 0, min_noise: float = 1e-4, callback=None, min_iter: int = 10,
+        loss_depth: int = 0):
     """Adam on softplus-raw (l, a^2, sigma^2) for `steps` steps (the paper's
     training loop: Adam, CG tolerance 1.0 with an iteration floor by default).
     Probes are redrawn every step from a seeded generator (standard normals z~
@@ -83,7 +85,7 @@ def fit(ctx, X, y, kernel: int, init_lengthscale, init_outputscale: float, init_
     raw_s = torch.tensor(softplus_inv(max(init_noise - min_noise, 1e-6)), dtype=torch.float64, requires_grad=True)
     opt = torch.optim.Adam([raw_l, raw_a, raw_s], lr=lr)
     cfg = FitConfig(ctx=ctx, kernel=kernel, rank=rank, tol=tol, max_iter=max_iter, min_iter=min_iter,
-                    precision=precision)
+                    precision=precision, loss_depth=loss_depth)
     gen = torch.Generator(device="cpu").manual_seed(seed)
     hist = []
     for step in range(steps):

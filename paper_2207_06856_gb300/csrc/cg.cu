@@ -195,7 +195,10 @@ scalar_kernel(int mode, int stable, const double* __restrict__ part, int nblk, i
                     S.gamma_s = pos ? acc.s : 0.0;
                     S.gamma_e = pos ? acc.e : 0;
                     S.gamma = val;
-                    S.gamma0 = val;
+                    // r_0^T z_0 of the first run only: it weights the SLQ quadrature
+                    // of the Lanczos process that run's step sizes describe, and a
+                    // true-residual restart (k > 0) must not overwrite it
+                    if (k == 0) S.gamma0 = val;
                     S.alpha = 0.0;
                     S.beta = 0.0;
                     S.iters = k;

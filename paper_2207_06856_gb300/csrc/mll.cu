@@ -212,9 +212,12 @@ int mll_run(Ctx* ctx, WsCarver& wc, const gp_hyp_t* hyp, const float* X, const f
     st.beta = beta.data();
     st.gamma0 = g0.data();
     st.lanczos_len = lz.data();
+    gp_cg_opts_t oo = *o;
+    const int depth = (flags >> 8) & 0xff;   // GP_MLL_SLQ_MIN_ITER
+    if ((flags & GP_MLL_WANT_LOGDET) && depth > oo.min_iter) oo.min_iter = depth < oo.max_iter ? depth : oo.max_iter;
     {
         WsCarver w2 = wc;
-        const int cs = cg_run(ctx, w2, hyp, X, N, B, R, U, pc, o, &st, s);
+        const int cs = cg_run(ctx, w2, hyp, X, N, B, R, U, pc, &oo, &st, s);
         if (cs != GP_OK && cs != GP_ERR_NOT_CONVERGED) return cs;
     }
     if (stats) {
@@ -307,6 +310,7 @@ int gp_mll_and_grad(gp_ctx* ctx, const gp_hyp_t* hyp, const float* X, const floa
     if (!ctx || !X || !y || !Z || !grad || !opts) return GP_ERR_INVALID;
     GPK_TRY(gpk::check_hyp(hyp));
     if (N < 1 || M < 1 || M > 31 || hyp->d > 32 || !(hyp->noise > 0.0)) return GP_ERR_INVALID;
+    if (flags & ~(GP_MLL_PRECOND_PROBES | GP_MLL_WANT_LOGDET | GP_MLL_SLQ_MIN_ITER(255))) return GP_ERR_INVALID;
     int prev = 0;
     cudaGetDevice(&prev);
     if (prev != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess) return GP_ERR_CUDA;

@@ -475,11 +475,14 @@ def slq_quadrature(alpha, beta, gamma0: float) -> float:
 def mll_and_grad(ctx: Context, hyp: Hyper, X, y, Z, precond: Precond | None = None, E=None,
                  precond_probes: bool = False, want_logdet: bool = True, tol: float = 1e-2, max_iter: int = 100,
                  precision="fp16", want_X: bool = False, return_U: bool = False, restarts: int = 4,
-                 check_precision="fp32", escalate: bool = True, min_iter: int = 0, stream=None):
+                 check_precision="fp32", escalate: bool = True, min_iter: int = 0, loss_depth: int = 0,
+                 stream=None):
     """gp_mll_and_grad.  X (N, d), y (N,), Z (M, N) probes [, E (M, rank) normals]
     -> (mll, grad (numpy, d + 2), grad_X or None, U or None, info).  min_iter: CG
     iterations run before the tolerance is tested (a loose tolerance such as the
-    training loop's 1.0 is otherwise met by x_0 = 0)."""
+    training loop's 1.0 is otherwise met by x_0 = 0).  loss_depth: with
+    want_logdet, the Lanczos depth (iterations of every column) the loss value
+    is taken from, whatever the tolerance (GP_MLL_SLQ_MIN_ITER)."""
     import torch
     N, d = X.shape
     M = Z.shape[0]
@@ -494,7 +497,8 @@ def mll_and_grad(ctx: Context, hyp: Hyper, X, y, Z, precond: Precond | None = No
         raise GPKError(GP_ERR_INVALID, "gp_mll_workspace_size")
     if need > ctx.workspace_bytes:
         ctx.reserve(need)
-    flags = (MLL_PRECOND_PROBES if precond_probes else 0) | (MLL_WANT_LOGDET if want_logdet else 0)
+    flags = (MLL_PRECOND_PROBES if precond_probes else 0) | (MLL_WANT_LOGDET if want_logdet else 0) | \
+        ((int(loss_depth) & 0xff) << 8)
     mll = ctypes.c_double(0.0)
     g = np.zeros(d + 2, np.float64)
     gX = torch.empty((N, d), dtype=torch.float32, device=X.device) if want_X else None

@@ -151,3 +151,88 @@ def test_workload_distributions_gradient(ctx, name):
     Uex = O.cholesky_solve(X, oh, B)
     ref = O.pseudo_loss_grad(X, oh, Uex, Z.T.astype(np.float64))
     assert _rel(g, ref) <= 1e-2, (g, ref)
+
+
+def test_mll_fp16_differentiation_inputs_n16384(ctx):
+    """The differentiation inputs (d = 18, ARD RBF, 8-component Gaussian
+    mixture, random-feature targets) at N = 16,384, where the dense FP64
+    oracle fits: the FP16 loss of gp_mll_and_grad (P-distributed probes,
+    rank-100 preconditioner, SLQ log-determinant, solves to 1e-3) within 1e-3
+    of the same-probe FP64 estimate, and its gradient within 1e-2 of the
+    same-probe FP64 estimator (Eq. approx) with converged FP64 solves."""
+    from oracle import cfp64 as C
+    from paper_2207_06856_gb300 import gpk
+    w = workloads.differentiation(N=16384)
+    X, y = w.X, w.y
+    N, d = X.shape
+    M, rank = 16, 100
+    rng = np.random.default_rng(17)
+    Zt = rng.standard_normal((M, N)).astype(np.float32)
+    E = rng.standard_normal((M, rank)).astype(np.float32)
+    hyp = gpk.Hyper(w.kernel, w.lengthscale, w.outputscale, w.noise)
+    Xd = _dev(X)
+    pc = gpk.pivchol(ctx, hyp, Xd, rank)
+    mll, g, _, U, info = gpk.mll_and_grad(ctx, hyp, Xd, _dev(y), _dev(Zt), precond=pc, E=_dev(E),
+                                          precond_probes=True, want_logdet=True, tol=1e-3, max_iter=1000,
+                                          precision="fp16", return_U=True)
+    ctx.check()
+    oh = O.Hyp("rbf", w.lengthscale.astype(np.float64), w.outputscale, w.noise)
+    L = pc.L.cpu().numpy().astype(np.float64).T                                  # the GPU's factor
+    s2 = w.noise
+    Zp = L @ E.T.astype(np.float64) + math.sqrt(s2) * Zt.T.astype(np.float64)   # N x M, E[zz^T] = P
+    pre = lambda r: O.precond_apply(L, s2, r)  # noqa: E731
+    Kt = O.ktilde_dense(X, oh)
+    res = O.cg_mbcg(lambda V: Kt @ V, np.column_stack([y.astype(np.float64), Zp]), precond=pre, tol=1e-9,
+                    max_iter=3000)
+    del Kt
+    est = [O.slq_quadrature(O.lanczos_tridiagonal(r.alphas, r.betas), r.gamma0) for r in res[1:]]
+    logdet = O.precond_logdet(L, s2) + float(np.mean(est))
+    ref = 0.5 * logdet + 0.5 * float(y.astype(np.float64) @ res[0].x) + 0.5 * N * math.log(2 * math.pi)
+    assert abs(mll - ref) <= 1e-3 * abs(ref), (mll, ref)
+    Uex = np.column_stack([r.x for r in res])
+    refg = C.pseudo_loss_grad(X, oh, Uex, Zp, W=pre(Zp))
+    assert _rel(g, refg) <= 1e-2, (g, refg)
+
+
+def test_mll_loss_depth_is_decoupled_from_tolerance(ctx):
+    """At the training tolerance (1.0, iteration floor 10) the solve stops after
+    10 iterations, too few Lanczos steps for the loss value; with
+    GP_MLL_SLQ_MIN_ITER(n) every column runs n iterations and the loss agrees
+    with the loss of converged solves (tol 1e-4) to 1e-3."""
+    from paper_2207_06856_gb300 import gpk
+    w = workloads.differentiation(N=4000)
+    N = w.X.shape[0]
+    M, rank = 16, 100
+    rng = np.random.default_rng(19)
+    Zt = _dev(rng.standard_normal((M, N)))
+    E = _dev(rng.standard_normal((M, rank)))
+    hyp = gpk.Hyper(w.kernel, w.lengthscale, w.outputscale, w.noise)
+    Xd, yd = _dev(w.X), _dev(w.y)
+    pc = gpk.pivchol(ctx, hyp, Xd, rank)
+    kw = dict(precond=pc, E=E, precond_probes=True, want_logdet=True, max_iter=400, precision="fp32")
+    conv, *_ = gpk.mll_and_grad(ctx, hyp, Xd, yd, Zt, tol=1e-4, **kw)
+    loose, _, _, _, i_loose = gpk.mll_and_grad(ctx, hyp, Xd, yd, Zt, tol=1.0, min_iter=10, **kw)
+    deep, _, _, _, i_deep = gpk.mll_and_grad(ctx, hyp, Xd, yd, Zt, tol=1.0, min_iter=10, loss_depth=200, **kw)
+    ctx.check()
+    assert np.all(i_deep["col_iters"] >= 200) and np.max(i_loose["col_iters"]) < 200
+    assert abs(deep - conv) <= 1e-3 * abs(conv), (deep, conv, loose)
+
+
+def test_kmvm_differentiation_workload_sampled_rows(ctx):
+    """The differentiation workload's MVM (N = 262,144, d = 18, ARD RBF, FP16
+    with the inputs carried as hi + lo): 64 sampled rows against exact FP64 rows."""
+    from oracle import cfp64 as C
+    from paper_2207_06856_gb300 import gpk
+    w = workloads.differentiation()
+    dev = torch.device("cuda:0")
+    V = np.random.default_rng(21).standard_normal((5, w.X.shape[0])).astype(np.float32)
+    hyp = gpk.Hyper(w.kernel, w.lengthscale, w.outputscale, w.noise)
+    out = gpk.kmvm(ctx, hyp, torch.from_numpy(w.X).to(dev), torch.from_numpy(V).to(dev), precision="fp16",
+                   add_noise=True)
+    ctx.check()
+    rows = np.sort(np.random.default_rng(22).choice(w.X.shape[0], 64, replace=False))
+    got = out[:, torch.from_numpy(rows).to(dev)].cpu().numpy().astype(np.float64)
+    oh = O.Hyp("rbf", w.lengthscale.astype(np.float64), w.outputscale, w.noise)
+    ref = C.kmvm(w.X, V.T.astype(np.float64), oh, rows=rows).T
+    err = np.max(np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1))
+    assert err <= 2e-3, err

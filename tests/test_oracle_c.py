@@ -108,3 +108,44 @@ def test_invalid_arguments_are_refused():
         C.kmvm(X, np.zeros((4, 0)), O.Hyp("rbf", np.ones(2)))
     assert C.threads() >= 1
     _ = C.kmvm(X, V, O.Hyp("rbf", np.ones(2)))
+
+
+@pytest.mark.parametrize("kern", list(O.KERNELS))
+def test_quad_form_grad_equals_numpy_oracle(kern):
+    rng = np.random.default_rng(8)
+    X = rng.standard_normal((150, 4))
+    U = rng.standard_normal((150, 3))
+    V = rng.standard_normal((150, 3))
+    h = O.Hyp(kern, rng.uniform(0.6, 1.8, 4), 1.2, 0.09)
+    ref, refX = O.quad_form_grad(X, h, U, V, wrt_X=True)
+    g, gX = C.quad_form_grad(X, h, U, V, wrt_X=True)
+    assert np.max(np.abs(g - ref)) <= 1e-10 * np.max(np.abs(ref))
+    assert np.max(np.abs(gX - refX)) <= 1e-10 * np.max(np.abs(refX))
+    Z = rng.standard_normal((150, 2))
+    Uf = rng.standard_normal((150, 3))
+    a = C.pseudo_loss_grad(X, h, Uf, Z)
+    b = O.pseudo_loss_grad(X, h, Uf, Z)
+    assert np.max(np.abs(a - b)) <= 1e-10 * np.max(np.abs(b))
+
+
+def test_quad_form_grad_finite_differences():
+    """d/da^2 and d/dl_m of u^T Ktilde v by central differences of the C MVM."""
+    rng = np.random.default_rng(9)
+    X = rng.standard_normal((120, 3))
+    u = rng.standard_normal((120, 1))
+    v = rng.standard_normal((120, 1))
+    ls = np.array([0.8, 1.1, 1.5])
+    h = O.Hyp("matern52", ls, 1.3, 0.1)
+    g, _ = C.quad_form_grad(X, h, u, v)
+    q = lambda hh: float(u[:, 0] @ C.kmvm(X, v, hh)[:, 0])   # noqa: E731
+    eps = 1e-6
+    for m in range(3):
+        lp, lm = ls.copy(), ls.copy()
+        lp[m] += eps
+        lm[m] -= eps
+        fd = (q(O.Hyp("matern52", lp, 1.3, 0.1)) - q(O.Hyp("matern52", lm, 1.3, 0.1))) / (2 * eps)
+        assert abs(fd - g[m]) <= 1e-6 * max(1.0, abs(fd))
+    fd = (q(O.Hyp("matern52", ls, 1.3 + eps, 0.1)) - q(O.Hyp("matern52", ls, 1.3 - eps, 0.1))) / (2 * eps)
+    assert abs(fd - g[3]) <= 1e-6 * max(1.0, abs(fd))
+    fd = (q(O.Hyp("matern52", ls, 1.3, 0.1 + eps)) - q(O.Hyp("matern52", ls, 1.3, 0.1 - eps))) / (2 * eps)
+    assert abs(fd - g[4]) <= 1e-6 * max(1.0, abs(fd))

@@ -420,3 +420,27 @@ def test_paper_float_format_numbers():
     assert abs(float(np.finfo(np.float32).tiny) - g["single_min_normal"]) < 1e-41
     assert abs(float(np.finfo(np.float16).tiny) - g["half_min_normal"]) < 1e-9
     assert abs(2.0 ** -24 - g["single_roundoff"]) < 1e-8
+
+
+def test_mbcg_equals_alg1_column_by_column():
+    """mBCG (App. A) runs Alg. 1 per column with per-column scalars: each
+    column's step sizes equal cg_standard's while rounding (the summation order
+    of the dot products differs) has not grown yet, the iteration counts agree
+    to one step, and both reach the Cholesky solution."""
+    rng = np.random.default_rng(31)
+    X = rng.standard_normal((120, 3))
+    h = O.Hyp("matern32", np.array([0.9, 1.2, 0.7]), 1.1, 0.5)
+    Kt = O.ktilde_dense(X, h)
+    L, _ = O.pivoted_cholesky(X, h, 10)
+    pre = lambda r: O.precond_apply(L, h.noise, r)   # noqa: E731
+    B = rng.standard_normal((120, 4))
+    B[:, 3] *= 1e-3                                    # scaled column: the same relative trajectory
+    res = O.cg_mbcg(lambda V: Kt @ V, B, precond=pre, tol=1e-8, max_iter=200)
+    exact = O.cholesky_solve(X, h, B)
+    for c in range(4):
+        ref = O.cg_standard(lambda v: Kt @ v, B[:, c], precond=pre, tol=1e-8, max_iter=200)
+        assert abs(res[c].iters - ref.iters) <= 1
+        np.testing.assert_allclose(res[c].alphas[:12], ref.alphas[:12], rtol=1e-9)
+        np.testing.assert_allclose(res[c].betas[:12], ref.betas[:12], rtol=1e-9)
+        assert abs(res[c].gamma0 - ref.gamma0) <= 1e-12 * abs(ref.gamma0)
+        assert np.linalg.norm(res[c].x - exact[:, c]) <= 1e-6 * np.linalg.norm(exact[:, c])
