@@ -302,7 +302,7 @@ def run_ours(args):
     arms = {}
     if not args.no_arms:
         for name, prec, alg, ro in [("fp32_plain_alg1", "fp32", "standard", "none"),
-                                    ("bf16_stable_alg2", "bf16", "stable", "pinv"),
+                                    ("bf16_hi_lo_stable_alg2", "bf16", "stable", "pinv"),
                                     ("fp16_split_tile_and_inputs_stable_alg2",
                                      gpk.FP16 | gpk.MVM_PSPLIT | gpk.MVM_XSPLIT, "stable", "pinv"),
                                     ("fp16_half_exp_stable_alg2", gpk.FP16 | gpk.MVM_HALF_EXP, "stable", "pinv"),
@@ -441,6 +441,43 @@ def run_kmvm(args):
                       "half_exp": bool(args.half_exp),
                       "launches": n,
                       "avg_launch_ms": ms / max(n, 1), "pairs_per_s": pairs / (ms / max(n, 1) / 1e3)}), flush=True)
+
+
+def run_vjp(args):
+    """The backward of the kernel MVM alone on the differentiation workload
+    (N = 262,144, d = 18, ARD RBF, 17 columns): the tensor-core FP16 backward
+    and the CUDA-core FP32 one, CUDA-event timed; pairs/s = N^2 / time."""
+    import torch
+    from paper_2207_06856_gb300 import gpk, workloads
+    w = workloads.differentiation(N=args.diff_n)
+    N = w.X.shape[0]
+    ctx = gpk.Context(0)
+    hyp = gpk.Hyper(w.kernel, w.lengthscale, w.outputscale, w.noise)
+    X = torch.from_numpy(w.X).cuda()
+    rng = np.random.default_rng(5)
+    U = torch.from_numpy(rng.standard_normal((17, N)).astype(np.float32)).cuda()
+    W = torch.from_numpy(rng.standard_normal((17, N)).astype(np.float32)).cuda()
+    res = {}
+    for prec in ("fp16", "fp32"):
+        for _ in range(2):
+            gpk.kmvm_vjp(ctx, hyp, X, U, W, want_X=True, precision=prec)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            gpk.kmvm_vjp(ctx, hyp, X, U, W, want_X=True, precision=prec)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        res[prec] = {"ms_per_backward": ms, "pairs_per_s": float(N) ** 2 / (ms * 1e-3)}
+    ctx.profile(True)
+    gpk.kmvm_vjp(ctx, hyp, X, U, W, want_X=True, precision="fp16")
+    kms, kn = ctx.profile_read()
+    ctx.profile(False)
+    res["fp16"]["kernel_ms"] = kms / max(kn, 1)
+    ctx.check()
+    print(json.dumps({"mode": "vjp", "N": N, "d": int(w.X.shape[1]), "R": 17, **res}), flush=True)
 
 
 def run_serve(args):
@@ -667,7 +704,7 @@ def main():
     ap.add_argument("--extra-diff-steps", type=int, default=4)
     ap.add_argument("--extra-serve-requests", type=int, default=96)
     ap.add_argument("--ref-iters", type=int, default=152)
-    ap.add_argument("--mode", default="solve", choices=["solve", "kmvm", "serve", "diff", "scale"])
+    ap.add_argument("--mode", default="solve", choices=["solve", "kmvm", "serve", "diff", "scale", "vjp"])
     ap.add_argument("--diff-steps", type=int, default=20)
     ap.add_argument("--diff-n", type=int, default=262144)
     ap.add_argument("--diff-tol", type=float, default=1.0)
@@ -690,6 +727,8 @@ def main():
         run_diff(args)
     elif args.mode == "scale":
         run_scale(args)
+    elif args.mode == "vjp":
+        run_vjp(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

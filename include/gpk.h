@@ -312,6 +312,24 @@ GPK_API size_t gp_kmvm_vjp_workspace_size(const gp_hyp_t* hyp, int64_t N, int R)
 GPK_API int gp_kmvm_vjp(gp_ctx* ctx, const gp_hyp_t* hyp, const float* X, int64_t N, const float* U,
                         const float* W, int R, double* grad_theta, float* grad_X, void* stream);
 
+/* The same gradient with a choice of arithmetic:
+ *   GP_PREC_FP32  the CUDA-core FP32 backward above (gp_kmvm_vjp);
+ *   GP_PREC_FP16  the tensor-core backward (flash-attention-backward shape):
+ *     S = X_i X_j^T and H = [u | w]_i [w | u]_j^T on tcgen05 (FP16 operands,
+ *     FP32 accumulation in TMEM), W' = a^2 k'(r^2) H elementwise (exp / sqrt on
+ *     the special function units), then W' [x / l, 1] on tcgen05 gives the row
+ *     sums and W' X from which every derivative follows (Eq. gradient: with
+ *     H = G + G^T symmetric, sum_ij a^2 k' G_ij (x_im - x_jm)^2 and
+ *     sum_j (G_ij + G_ji) a^2 k' (x_im - x_jm) are sums of W' (x_im - x_jm)).
+ *     RBF, Matern-3/2 and Matern-5/2 with d <= 31 (d <= 20 when d > 12, where
+ *     the inputs are carried as hi + lo); Matern-1/2 (k' ~ 1/r, singular at
+ *     coincident points) and wider inputs return GP_ERR_UNSUPPORTED.
+ * gp_mll_and_grad uses the FP16 backward whenever its solve's MVM precision is
+ * not FP32 and the shape is supported. */
+GPK_API size_t gp_kmvm_vjp_prec_workspace_size(const gp_hyp_t* hyp, int64_t N, int R, int precision);
+GPK_API int gp_kmvm_vjp_prec(gp_ctx* ctx, const gp_hyp_t* hyp, const float* X, int64_t N, const float* U,
+                             const float* W, int R, int precision, double* grad_theta, float* grad_X, void* stream);
+
 /* ---- S7: stochastic Lanczos quadrature from CG step sizes (host) -----------
  * out = gamma0 * e1^T log(T) e1 for the Lanczos tridiagonal T of a CG run
  * with step sizes alpha[0..J) and beta[0..J-1) (beta[k] = beta_{k+1} of

@@ -299,6 +299,12 @@ int vjp_run(Ctx* ctx, WsCarver& wc, const gp_hyp_t* hyp, const float* X, int64_t
             int R, double* grad_theta_host, float* gX_dev, cudaStream_t s);
 int launch_scale_cols(Ctx* ctx, const float* src, int64_t N, int dp, int d, const float* ls_host, float* dst,
                       cudaStream_t s);
+// Tensor-core backward (vjp_tc.cu): RBF / Matern-3/2 / Matern-5/2, d <= 31, R <= 32,
+// FP16 operands with FP32 accumulation.
+bool vjp_tc_supported(const gp_hyp_t* hyp, int R);
+size_t vjp_tc_workspace(const Ctx* ctx, const gp_hyp_t* hyp, int64_t N, int R);
+int vjp_tc_run(Ctx* ctx, WsCarver& wc, const gp_hyp_t* hyp, const float* X, int64_t N, const float* U,
+               const float* W, int R, double* grad_theta_host, float* gX_dev, cudaStream_t s);
 int slq_quadrature_host(const double* alpha, const double* beta, int J, double gamma0, double* out);
 
 }  // namespace gpk

@@ -173,7 +173,8 @@ size_t mll_workspace(const Ctx* ctx, const gp_hyp_t* hyp, int64_t N, int M, int 
     c.take<double>(4);
     size_t s = c.off;
     const size_t cgw = cg_workspace(ctx, hyp, N, M + 1, rank, o);
-    const size_t vw = vjp_workspace(N, hyp->d, M + 1);
+    const bool tc = (o->precision & 0xff) != GP_PREC_FP32 && vjp_tc_supported(hyp, M + 1);
+    const size_t vw = tc ? vjp_tc_workspace(ctx, hyp, N, M + 1) : vjp_workspace(N, hyp->d, M + 1);
     const size_t ww = rank > 0 ? woodbury_workspace(ctx, N, rank, M + 1) : 0;
     size_t m = cgw > vw ? cgw : vw;
     m = m > ww ? m : ww;
@@ -242,8 +243,12 @@ int mll_run(Ctx* ctx, WsCarver& wc, const gp_hyp_t* hyp, const float* X, const f
     ctx->launches++;
     if (cudaGetLastError() != cudaSuccess) return GP_ERR_CUDA;
     {
+        // the backward runs on the tensor cores in FP16 when the solve's MVM does
         WsCarver w2 = wc;
-        GPK_TRY(vjp_run(ctx, w2, hyp, X, N, Uo, Wo, R, grad, gradX, s));
+        if ((o->precision & 0xff) != GP_PREC_FP32 && vjp_tc_supported(hyp, R))
+            GPK_TRY(vjp_tc_run(ctx, w2, hyp, X, N, Uo, Wo, R, grad, gradX, s));
+        else
+            GPK_TRY(vjp_run(ctx, w2, hyp, X, N, Uo, Wo, R, grad, gradX, s));
     }
 
     // ---- loss value (Eq. loss) with the SLQ log-determinant ----

@@ -318,4 +318,32 @@ int gp_kmvm_vjp(gp_ctx* ctx, const gp_hyp_t* hyp, const float* X, int64_t N, con
     return st;
 }
 
+size_t gp_kmvm_vjp_prec_workspace_size(const gp_hyp_t* hyp, int64_t N, int R, int precision) {
+    if (gpk::check_hyp(hyp) != GP_OK || N < 1 || R < 1 || R > 32 || hyp->d > 32) return 0;
+    if (precision == GP_PREC_FP32) return gpk::vjp_workspace(N, hyp->d, R);
+    if (precision != GP_PREC_FP16 || !gpk::vjp_tc_supported(hyp, R)) return 0;
+    gpk::Ctx probe;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&probe.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) probe.num_sms = 148;
+    return gpk::vjp_tc_workspace(&probe, hyp, N, R);
+}
+
+int gp_kmvm_vjp_prec(gp_ctx* ctx, const gp_hyp_t* hyp, const float* X, int64_t N, const float* U, const float* W,
+                     int R, int precision, double* grad_theta, float* grad_X, void* stream) {
+    if (precision == GP_PREC_FP32) return gp_kmvm_vjp(ctx, hyp, X, N, U, W, R, grad_theta, grad_X, stream);
+    if (!ctx || !X || !U || !W || !grad_theta) return GP_ERR_INVALID;
+    GPK_TRY(gpk::check_hyp(hyp));
+    if (N < 1 || R < 1 || R > 32 || hyp->d > 32) return GP_ERR_INVALID;
+    if (precision != GP_PREC_FP16) return GP_ERR_INVALID;
+    if (!gpk::vjp_tc_supported(hyp, R)) return GP_ERR_UNSUPPORTED;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess) return GP_ERR_CUDA;
+    gpk::WsCarver wc(ctx->ws, ctx->ws_bytes);
+    int st = gpk::vjp_tc_run(ctx, wc, hyp, X, N, U, W, R, grad_theta, grad_X, (cudaStream_t)stream);
+    if (prev != ctx->device) cudaSetDevice(prev);
+    return st;
+}
+
 }  // extern "C"

@@ -439,24 +439,34 @@ MLL_PRECOND_PROBES = 0x1
 MLL_WANT_LOGDET = 0x2
 
 
-def kmvm_vjp(ctx: Context, hyp: Hyper, X, U, W, want_X: bool = False, stream=None):
-    """gp_kmvm_vjp: gradient of sum_c u_c^T Ktilde w_c w.r.t. (l_1..l_d, a^2, sigma^2)
-    (numpy, d + 2) and optionally X (CUDA tensor N x d).  U, W: (R, N)."""
+def kmvm_vjp(ctx: Context, hyp: Hyper, X, U, W, want_X: bool = False, precision="fp32", stream=None):
+    """gp_kmvm_vjp / gp_kmvm_vjp_prec: gradient of sum_c u_c^T Ktilde w_c w.r.t.
+    (l_1..l_d, a^2, sigma^2) (numpy, d + 2) and optionally X (CUDA tensor N x d).
+    U, W: (R, N).  precision "fp32": the CUDA-core backward; "fp16": the
+    tensor-core backward (RBF / Matern-3/2 / Matern-5/2)."""
     import torch
     N, d = X.shape
     R = U.shape[0]
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     h = hyp.c()
-    need = int(lib().gp_kmvm_vjp_workspace_size(ctypes.byref(h), N, R))
+    fw = lib().gp_kmvm_vjp_prec_workspace_size
+    fw.restype = ctypes.c_size_t
+    fw.argtypes = [ctypes.POINTER(_Hyp), _c_i64, _c_int, _c_int]
+    need = int(fw(ctypes.byref(h), N, R, prec))
     if need == 0:
-        raise GPKError(GP_ERR_INVALID, "gp_kmvm_vjp_workspace_size")
+        raise GPKError(GP_ERR_UNSUPPORTED if prec != FP32 else GP_ERR_INVALID, "gp_kmvm_vjp_prec_workspace_size")
     if need > ctx.workspace_bytes:
         ctx.reserve(need)
     g = np.zeros(d + 2, np.float64)
     gX = torch.empty((N, d), dtype=torch.float32, device=X.device) if want_X else None
-    st = lib().gp_kmvm_vjp(ctx.ptr, ctypes.byref(h), _dev_ptr(X, "X", (N, d)), N, _dev_ptr(U, "U", (R, N)),
-                           _dev_ptr(W, "W", (R, N)), R, g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                           int(gX.data_ptr()) if gX is not None else None, _stream_ptr(stream))
-    _check(st, "gp_kmvm_vjp")
+    fn = lib().gp_kmvm_vjp_prec
+    fn.restype = _c_int
+    fn.argtypes = [_c_void_p, ctypes.POINTER(_Hyp), _c_void_p, _c_i64, _c_void_p, _c_void_p, _c_int, _c_int,
+                   _c_void_p, _c_void_p, _c_void_p]
+    st = fn(ctx.ptr, ctypes.byref(h), _dev_ptr(X, "X", (N, d)), N, _dev_ptr(U, "U", (R, N)),
+            _dev_ptr(W, "W", (R, N)), R, prec, g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            int(gX.data_ptr()) if gX is not None else None, _stream_ptr(stream))
+    _check(st, "gp_kmvm_vjp_prec")
     return g, gX
 
 

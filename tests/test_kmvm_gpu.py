@@ -304,3 +304,23 @@ def test_kmvm_half_exp_unsupported(ctx, case):
     X, V, _, ls, a2, s2 = workloads.random_problem(300, d, 3, seed=2, kernel=kern)
     with pytest.raises(gpk.GPKError):
         _run(ctx, X, V, kern, ls, a2, s2, prec, flags=fl)
+
+
+@pytest.mark.parametrize("where", ["V", "X"])
+def test_kmvm_nonfinite_input_is_reported(ctx, where):
+    """A NaN in the right-hand sides (their column scale) or in the inputs
+    (their FP16 norm terms) is recorded on the device and reported as
+    GP_ERR_NONFINITE by the context check, not returned as a silent result."""
+    from paper_2207_06856_gb300 import gpk
+    X, V, kern, ls, a2, s2 = workloads.random_problem(500, 6, 3, seed=41)
+    if where == "V":
+        V[1, 17] = np.nan
+    else:
+        X[33, 2] = np.nan
+    dev = torch.device("cuda:0")
+    gpk.kmvm(ctx, gpk.Hyper(kern, ls, a2, s2), torch.from_numpy(X).to(dev), torch.from_numpy(V).to(dev),
+             precision="fp16", add_noise=True)
+    with pytest.raises(gpk.GPKError) as ei:
+        ctx.check()
+    assert ei.value.status == gpk.GP_ERR_NONFINITE
+    ctx.check()   # the word was cleared

@@ -236,3 +236,51 @@ def test_kmvm_differentiation_workload_sampled_rows(ctx):
     ref = C.kmvm(w.X, V.T.astype(np.float64), oh, rows=rows).T
     err = np.max(np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1))
     assert err <= 2e-3, err
+
+
+VJP_TC_SHAPES = [(300, 3, 2), (1000, 8, 17), (777, 18, 5), (4097, 8, 17), (2000, 12, 32), (129, 20, 1)]
+
+
+@pytest.mark.parametrize("kern", [0, 1, 3])
+@pytest.mark.parametrize("shape", VJP_TC_SHAPES)
+def test_vjp_tensor_core_matches_oracle(ctx, kern, shape):
+    """The tensor-core backward (FP16 S, H = [u|w][w|u]^T and W' = a^2 k' H,
+    FP32 accumulation) against the FP64 bilinear-form gradient: <= 1e-2
+    relative, the gradient tolerance, for the hyperparameters and for X."""
+    from paper_2207_06856_gb300 import gpk
+    N, d, R = shape
+    X, V, _, ls, a2, s2 = workloads.random_problem(N, d, R, seed=N + 7 * d, kernel=kern)
+    U = np.random.default_rng(N + 1).standard_normal((R, N)).astype(np.float32)
+    hyp = gpk.Hyper(kern, ls, a2, s2)
+    g, gX = gpk.kmvm_vjp(ctx, hyp, _dev(X), _dev(U), _dev(V), want_X=True, precision="fp16")
+    ctx.check()
+    ref, refX = O.quad_form_grad(X, O.Hyp(KNAME[kern], ls, a2, s2), U.T, V.T, wrt_X=True)
+    assert _rel(g, ref) <= 1e-2, (g, ref)
+    assert _rel(gX.cpu().numpy(), refX) <= 1e-2
+
+
+def test_vjp_tensor_core_refuses_matern12(ctx):
+    from paper_2207_06856_gb300 import gpk
+    X, V, _, ls, a2, s2 = workloads.random_problem(300, 3, 2, seed=3, kernel=2)
+    with pytest.raises(gpk.GPKError):
+        gpk.kmvm_vjp(ctx, gpk.Hyper(2, ls, a2, s2), _dev(X), _dev(V), _dev(V), precision="fp16")
+
+
+def test_vjp_tensor_core_differentiation_inputs_n16384(ctx):
+    """The differentiation inputs (d = 18: inputs as hi + lo, k_pad 64) at
+    N = 16,384 with the 17 columns of the pseudo-loss: against the oracle's
+    matrix-free FP64 gradient, hyperparameters and X."""
+    from oracle import cfp64 as C
+    from paper_2207_06856_gb300 import gpk
+    w = workloads.differentiation(N=16384)
+    N = w.X.shape[0]
+    rng = np.random.default_rng(23)
+    U = rng.standard_normal((17, N)).astype(np.float32)
+    V = rng.standard_normal((17, N)).astype(np.float32)
+    hyp = gpk.Hyper(w.kernel, w.lengthscale, w.outputscale, w.noise)
+    g, gX = gpk.kmvm_vjp(ctx, hyp, _dev(w.X), _dev(U), _dev(V), want_X=True, precision="fp16")
+    ctx.check()
+    oh = O.Hyp("rbf", w.lengthscale.astype(np.float64), w.outputscale, w.noise)
+    ref, refX = C.quad_form_grad(w.X, oh, U.T, V.T, wrt_X=True)
+    assert _rel(g, ref) <= 1e-2, (g, ref)
+    assert _rel(gX.cpu().numpy(), refX) <= 1e-2

@@ -37,17 +37,16 @@ def gpk():
 @pytest.mark.gpu
 def test_serve_fp32_matches_exact_posterior_mean(gpk):
     """FP32 MVMs, CG to 1e-6: mu* = K(X*, X) Ktilde^{-1} y against the oracle's
-    Cholesky solve, within the first-order perturbation bound of the served
-    arithmetic: mu - mu_exact = K* Ktilde^{-1} r_true + dK* v with
-    ||r_true|| <= rel_resid ||y|| + ||dKtilde v||, where dKtilde v and dK* v are
-    the FP32 MVM's own errors (measured on the device at the exact weights v;
-    the reported residual is computed with the same FP32 operator, so it cannot
-    see them).  Factor 2: the solver meets those errors at its iterates, not at
-    v.  On these requests the bound is about 1e-4 relative."""
+    Cholesky solve, within the first-order perturbation bound of FP32
+    arithmetic alone: mu - mu_exact = K* Ktilde^{-1} r_true + dK* v with
+    ||r_true|| <= rel_resid ||y|| + ||dKtilde v||, and each FP32 MVM errs by at
+    most EPS32 = 1e-5 of its result (the FP32 MVM tolerance the MVM parity tests
+    establish against the FP64 oracle).  Every norm is taken in FP64 from the
+    oracle; nothing in the bound comes from the device.  Factor 2: the solver
+    meets those errors at its iterates, not at v."""
+    EPS32 = 1e-5
     srv = gpk.Server(0, arena_bytes=1 << 30, max_slots=4, rank=20, precision="fp32", mean_precision="fp32",
                      tol=1e-6, max_iter=600)
-    ctx = gpk.Context(0)
-    dev = torch.device("cuda:0")
     try:
         reqs = _requests(6, seed=3)
         futs = [srv.submit(_hyp(gpk, r), r.X, r.y, r.Xstar) for r in reqs]
@@ -61,18 +60,11 @@ def test_serve_fp32_matches_exact_posterior_mean(gpk):
             v = np.linalg.solve(Kt, y)
             ref = Ks @ v
             A = np.linalg.solve(Kt, Ks.T).T          # K* Ktilde^{-1} (Ktilde symmetric)
-            Xd = torch.from_numpy(r.X).to(dev)
-            vd = torch.from_numpy(v.astype(np.float32)[None, :]).to(dev)
-            kv = gpk.kmvm(ctx, _hyp(gpk, r), Xd, vd, precision="fp32", add_noise=True).cpu().numpy()[0]
-            ksv = gpk.kmvm(ctx, _hyp(gpk, r), torch.from_numpy(r.Xstar).to(dev), vd, Xc=Xd, precision="fp32",
-                           add_noise=False).cpu().numpy()[0]
-            e_t = np.linalg.norm(kv - Kt @ v)
-            e_s = np.linalg.norm(ksv - ref)
-            bound = np.linalg.norm(A, 2) * (st["rel_resid"] * np.linalg.norm(y) + e_t) + e_s
+            bound = np.linalg.norm(A, 2) * (st["rel_resid"] * np.linalg.norm(y) + EPS32 * np.linalg.norm(Kt @ v)) \
+                + EPS32 * np.linalg.norm(ref)
             err = np.linalg.norm(mean - ref)
-            assert err <= 2.0 * bound + 1e-6 * np.linalg.norm(ref), (r.rid, r.X.shape, err, bound)
+            assert err <= 2.0 * bound, (r.rid, r.X.shape, err, bound)
     finally:
-        ctx.close()
         srv.close()
 
 
