@@ -419,7 +419,14 @@ def run_kmvm(args):
     B = torch.from_numpy(w.rhs()).cuda()
     out = torch.empty_like(B)
     fl = (gpk.MVM_ONE_TILE if args.one_tile else 0) | (gpk.MVM_PSPLIT if args.psplit else 0) | \
-        (gpk.MVM_HALF_EXP if args.half_exp else 0)
+        (gpk.MVM_HALF_EXP if args.half_exp else 0) | (gpk.MVM_SKIP_TILES if args.skip_tiles else 0)
+    if args.clustered:
+        # compact-support case: 16 clusters of 4,096 points (d = 8, within-cluster std 0.3 lengthscales,
+        # centres 20 lengthscales apart), stored cluster by cluster
+        rng = np.random.default_rng(9)
+        cen = rng.standard_normal((16, 8)) * 20.0
+        Xc = np.concatenate([c + 0.3 * rng.standard_normal((4096, 8)) for c in cen]).astype(np.float32)
+        X = torch.from_numpy(Xc).cuda()
     for _ in range(args.warmup):
         gpk.kmvm(ctx, hyp, X, B, precision=args.precision, add_noise=True, out=out, flags=fl)
     torch.cuda.synchronize()
@@ -436,7 +443,12 @@ def run_kmvm(args):
         ms, n = e0.elapsed_time(e1), args.steps
     ctx.check()
     pairs = float(w.N) ** 2
+    ev, tot = gpk.kmvm_tile_count(ctx, hyp, X, precision=args.precision, flags=fl) if args.precision != "fp32" \
+        else (1, 1)
     print(json.dumps({"mode": "kmvm", "precision": args.precision, "kernel": args.kernel,
+                      "inputs": "clustered (16 clusters)" if args.clustered else "precision workload",
+                      "skip_tiles": bool(args.skip_tiles), "evaluated_fraction": ev / tot,
+                      "evaluated_pairs_per_s": pairs * ev / tot / (ms / max(n, 1) / 1e3),
                       "engine": "one-tile" if args.one_tile else "pair", "psplit": bool(args.psplit),
                       "half_exp": bool(args.half_exp),
                       "launches": n,
@@ -713,6 +725,8 @@ def main():
     ap.add_argument("--one-tile", action="store_true", help="kmvm mode: the one-row-tile tensor-core engine")
     ap.add_argument("--psplit", action="store_true", help="kmvm mode: FP16 kernel tile as hi + lo")
     ap.add_argument("--half-exp", action="store_true", help="kmvm mode: FP16 exp2 argument and exponential")
+    ap.add_argument("--skip-tiles", action="store_true", help="kmvm mode: compact-support tile skipping")
+    ap.add_argument("--clustered", action="store_true", help="kmvm mode: clustered inputs (16 far-apart clusters)")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-arena-gb", type=float, default=48.0)

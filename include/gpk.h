@@ -93,6 +93,12 @@ extern "C" {
                                        FP16 (ex2.approx.f16x2), the paper's
                                        half-precision kernel evaluation (Sec. 4.1);
                                        pair engine, d <= 12 without input split  */
+#define GP_MVM_SKIP_TILES  0x20000  /* compact support (Sec. 3.1, Fig. 2c): skip the
+                                       tile pairs whose operand bounding boxes put
+                                       every kernel value below half the smallest
+                                       subnormal of the kernel tile's format, where
+                                       it rounds to an exact 0 (bit-identical
+                                       result); pair engine, FP16 / BF16            */
 #define GP_MVM_ONE_TILE     0x4000  /* tensor-core MVM on the one-row-tile engine
                                        (P V with M = 128 rows, N = R) instead of
                                        the default pair engine (transposed
@@ -165,6 +171,13 @@ GPK_API size_t gp_kmvm_workspace_size(const gp_hyp_t* hyp, int64_t Nr, int64_t N
 GPK_API int gp_kmvm(gp_ctx* ctx, const gp_hyp_t* hyp,
             const float* Xr, int64_t Nr, const float* Xc, int64_t Nc,
             const float* V, int R, float* out, int flags, void* stream);
+
+/* Evaluated and total (row-tile pair, column tile) entries of the MVM that
+ * gp_kmvm would run for these arguments with GP_MVM_SKIP_TILES (without the
+ * flag every entry is evaluated).  Prepares the operands in the context's
+ * workspace; synchronises the stream.  One entry = 256 x 128 kernel pairs. */
+GPK_API int gp_kmvm_tile_count(gp_ctx* ctx, const gp_hyp_t* hyp, const float* Xr, int64_t Nr, const float* Xc,
+                               int64_t Nc, int flags, int64_t* evaluated, int64_t* total, void* stream);
 
 /* ---- kernel MVM without any allocation -------------------------------------
  * gp_kmvm_noalloc computes exactly what gp_kmvm computes (same arguments and

@@ -177,4 +177,29 @@ int gp_kmvm(gp_ctx* ctx, const gp_hyp_t* hyp, const float* Xr, int64_t Nr, const
     return kop_apply(ctx, op, V, R, out, Nr, add_noise, s);
 }
 
+int gp_kmvm_tile_count(gp_ctx* ctx, const gp_hyp_t* hyp, const float* Xr, int64_t Nr, const float* Xc, int64_t Nc,
+                       int flags, int64_t* evaluated, int64_t* total, void* stream) {
+    if (!ctx || !Xr || !Xc || !evaluated || !total) return GP_ERR_INVALID;
+    GPK_TRY(check_kmvm_args(hyp, Nr, Nc, 1, flags));
+    if ((flags & 0xff) == GP_PREC_FP32) return GP_ERR_UNSUPPORTED;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return GP_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    WsCarver wc(ctx->ws, ctx->ws_bytes);
+    KOp op;
+    GPK_TRY(kop_prepare(ctx, wc, op, hyp, Xr, Nr, Xc, Nc, 1, flags & ~GP_MVM_ADD_NOISE, s));
+    if (op.tp.engine != 1) return GP_ERR_UNSUPPORTED;
+    *total = (int64_t)op.tp.n_it * op.tp.n_jt;
+    if (!op.skip) {
+        *evaluated = *total;
+        return GP_OK;
+    }
+    unsigned long long c = 0;
+    if (cudaMemcpyAsync(&c, op.skip_count, sizeof(c), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return GP_ERR_CUDA;
+    *evaluated = (int64_t)c;
+    return GP_OK;
+}
+
 }  // extern "C"

@@ -152,7 +152,7 @@ TcPlan tp_plan(const Ctx* ctx, int64_t Nr, int64_t Nc, int R, int k_pad, int vsp
 size_t tp_partial_floats(const TcPlan& p);
 int launch_kmvm_tp(Ctx* ctx, const TcPlan& plan, const OperandLayout& L, const MvmArgs& a, const CUtensorMap& tmA,
                    const CUtensorMap& tmB, const CUtensorMap& tmV, const float* outscale, float* partial,
-                   cudaStream_t s);
+                   const uint32_t* mask, cudaStream_t s);
 
 // SIMT FP32 engine (kmvm_simt.cu).  Scaled FP32 inputs with row stride dp.
 struct SimtPlan {
@@ -189,6 +189,12 @@ struct KOp {
     unsigned* bbox = nullptr;
     float* partial = nullptr;
     CUtensorMap tmA, tmB, tmV;
+    // compact-support tile skipping (GP_MVM_SKIP_TILES, pair engine)
+    bool skip = false;
+    uint32_t* mask = nullptr;
+    float* rbox = nullptr;
+    float* cbox = nullptr;
+    unsigned long long* skip_count = nullptr;
 };
 size_t kop_workspace(const Ctx* ctx, const gp_hyp_t* hyp, int64_t Nr, int64_t Nc, int R, int flags, bool square);
 int kop_prepare(Ctx* ctx, WsCarver& wc, KOp& op, const gp_hyp_t* hyp, const float* Xr, int64_t Nr,
@@ -199,6 +205,12 @@ int kop_apply(Ctx* ctx, KOp& op, const float* V, int R, float* out, int64_t ld_o
 // Tensor-map helper (driver entry point fetched through the runtime).
 int encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uint64_t inner, uint64_t outer,
                    uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle swz);
+
+// Tile skipping (skip.cu): -s*, the mask's size in words, and its preparation
+// (bounding boxes of the operand tiles, then the mask and its popcount).
+double skip_threshold(int kernel, int prec);
+size_t skip_words(const TcPlan& p);
+int prepare_skip(Ctx* ctx, KOp& op, cudaStream_t s);
 
 // Hyperparameter validation shared by the entry points.
 int check_hyp(const gp_hyp_t* hyp);

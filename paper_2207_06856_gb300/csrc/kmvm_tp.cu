@@ -80,6 +80,8 @@ struct TpParams {
     int diag;             // square Matern-1/2 operator: P_ii = 0 on chip (exact diagonal added later)
     int64_t ld_part;      // n_ip * 256
     float* partial;       // [n_split][rv][ld_part]
+    const uint32_t* mask; // tile skipping: bit jt of word ip * mask_words + jt / 32 set = evaluate, or null
+    int mask_words;
     int* err;
     uint64_t limit_ns;
 };
@@ -105,6 +107,12 @@ __device__ __forceinline__ void item_range(const TpParams& p, int item, int& ip,
     sp = item / p.n_ip;
     j0 = (int)(((int64_t)sp * p.n_jt) / p.n_split);
     j1 = (int)(((int64_t)(sp + 1) * p.n_jt) / p.n_split);
+}
+
+// Whether the column tile jt of row-tile pair ip is evaluated (compact support:
+// a cleared bit means every kernel value of the pair rounds to zero).
+__device__ __forceinline__ bool tile_on(const TpParams& p, int ip, int jt) {
+    return !p.mask || ((__ldg(p.mask + (int64_t)ip * p.mask_words + (jt >> 5)) >> (jt & 31)) & 1u);
 }
 
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
@@ -133,6 +141,7 @@ __device__ void tp_producer(const TpParams& p, const CUtensorMap* tmA, const CUt
         ptx::tma_load_2d(sX + xbytes, tmA, &bars.xi_full[xb], 0, ip * kPairRows + kBM);
         ++xi_loads;
         for (int jt = j0; jt < j1; ++jt) {
+            if (!tile_on(p, ip, jt)) continue;
             const uint32_t st = fills % S, u = fills / S;
             if (u > 0 && !ptx::mbar_wait(&bars.empty[st], (u - 1) & 1, p.limit_ns)) { ok = false; break; }
             uint8_t* sx = sSt + st * (xbytes + vtbytes);
@@ -185,13 +194,13 @@ __device__ void tp_mma_s(const TpParams& p, TpBarriers& bars, const uint8_t* sSt
     for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x, ++ic) {
         int ip, sp, j0, j1;
         item_range(p, item, ip, sp, j0, j1);
-        const uint32_t T = (uint32_t)(j1 - j0);
         const int xb = p.xi_bufs == 2 ? (ic & 1) : 0;
         const int use = p.xi_bufs == 2 ? (ic >> 1) : ic;
         if (!warp_wait(&bars.xi_full[xb], use & 1, p.limit_ns)) { ok = false; break; }
         ptx::tc_fence_after();
         const uint32_t aXi = ptx::smem_u32(sXi) + (uint32_t)xb * 2u * xbytes;
-        for (uint32_t t = 0; t < T; ++t, ++g) {
+        for (int jt = j0; jt < j1; ++jt) {
+            if (!tile_on(p, ip, jt)) continue;
             if (g > 0 && !(warp_wait(&bars.s_empty[0], (g - 1) & 1, p.limit_ns) &&
                            warp_wait(&bars.s_empty[1], (g - 1) & 1, p.limit_ns))) { ok = false; break; }
             if (!warp_wait(&bars.full[st], ph, p.limit_ns)) { ok = false; break; }
@@ -206,9 +215,11 @@ __device__ void tp_mma_s(const TpParams& p, TpBarriers& bars, const uint8_t* sSt
                 }
                 ptx::mma_commit_elect(&bars.s_full[w]);
             }
-            if (t + 1 == T) ptx::mma_commit_elect(&bars.xi_empty[xb]);   // last use of the row tiles
             if (++st == S) { st = 0; ph ^= 1u; }
+            ++g;
         }
+        if (!ok) break;
+        ptx::mma_commit_elect(&bars.xi_empty[xb]);   // the row tiles' last use in this item
     }
     ptx::mma_commit_elect(&bars.drain[0]);
     warp_wait(&bars.drain[0], 0, p.limit_ns);
@@ -233,9 +244,10 @@ __device__ void tp_mma_pv(const TpParams& p, TpBarriers& bars, const uint8_t* sS
     for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x, ++ic) {
         int ip, sp, j0, j1;
         item_range(p, item, ip, sp, j0, j1);
-        const uint32_t T = (uint32_t)(j1 - j0);
-        for (uint32_t t = 0; t < T && ok; ++t, ++g) {
-            if (t == 0 && ic > 0 && !warp_wait(&bars.o_empty, (ic - 1) & 1, p.limit_ns)) { ok = false; break; }
+        if (ic > 0 && !warp_wait(&bars.o_empty, (ic - 1) & 1, p.limit_ns)) { ok = false; break; }
+        uint32_t t = 0;   // evaluated tiles of this item
+        for (int jt = j0; jt < j1 && ok; ++jt) {
+            if (!tile_on(p, ip, jt)) continue;
             // Vt_j of this stage: landed before S of this tile was issued (already complete)
             if (!warp_wait(&bars.full[st], ph, p.limit_ns)) { ok = false; break; }
             for (uint32_t kb = 0; kb < (PSPLIT ? 2u : 1u); ++kb) {
@@ -260,6 +272,8 @@ __device__ void tp_mma_pv(const TpParams& p, TpBarriers& bars, const uint8_t* sS
             if (!ok) break;
             ptx::mma_commit_elect(&bars.empty[st]);             // X_j and Vt_j of this stage are consumed
             if (++st == S) { st = 0; ph ^= 1u; }
+            ++t;
+            ++g;
         }
         if (!ok) break;
         ptx::mma_commit_elect(&bars.o_full);
@@ -354,14 +368,15 @@ __device__ void tp_epilogue(const TpParams& p, TpBarriers& bars, const uint8_t* 
     for (int item = blockIdx.x; item < p.n_items; item += gridDim.x, ++ic) {
         int ip, sp, j0, j1;
         item_range(p, item, ip, sp, j0, j1);
-        const uint32_t T = (uint32_t)(j1 - j0);
         const int it = 2 * ip + tl;   // this warpgroup's row tile
-        for (uint32_t t = 0; t < T; ++t) {
+        uint32_t t = 0;               // evaluated tiles of this item
+        for (int jt = j0; jt < j1; ++jt) {
+            if (!tile_on(p, ip, jt)) continue;
             const uint32_t g = gt + t;
             if (!__all_sync(0xffffffffu, ptx::mbar_wait(&bars.s_full[tl], g & 1, p.limit_ns))) { ok = false; break; }
             ptx::tc_fence_after();
             const uint32_t tS = tmem + lane_off + (uint32_t)tl * 128u + (uint32_t)ch * 64u;
-            const bool dtile = (KIND == GP_KERNEL_MATERN12) && p.diag && (j0 + (int)t == it);
+            const bool dtile = (KIND == GP_KERNEL_MATERN12) && p.diag && (jt == it);
             uint32_t ra[32], rb[HS ? 1 : 32];
             if constexpr (HS) {
                 ptx::tmem_ld32_pack16(tS, ra);     // 64 FP16 columns in 32 registers
@@ -405,8 +420,8 @@ __device__ void tp_epilogue(const TpParams& p, TpBarriers& bars, const uint8_t* 
             ptx::fence_proxy_async_smem();        // P stores -> visible to the tensor core
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(&bars.p_full[buf]);
+            ++t;
         }
-        if (!ok) break;
         if (!ok) break;
         // O^T read-out: lanes [0, rv) are the rows of Vt; this warpgroup's 64 columns.
         if (!__all_sync(0xffffffffu, ptx::mbar_wait(&bars.o_full, ic & 1, p.limit_ns))) { ok = false; break; }
@@ -416,9 +431,14 @@ __device__ void tp_epilogue(const TpParams& p, TpBarriers& bars, const uint8_t* 
             float* dst = p.partial + ((int64_t)sp * p.rv + r) * p.ld_part + (int64_t)ip * kPairRows + tl * kBM + ch * 64;
             for (int h = 0; h < 2; ++h) {
                 uint32_t o[32];
-                ptx::tmem_ld32(tmem + lane_off + kTmemO + (uint32_t)(tl * kBM + ch * 64 + h * 32), o);
-                ptx::tmem_wait_ld();
-                ptx::tmem_reg_fence(o);
+                if (t > 0) {
+                    ptx::tmem_ld32(tmem + lane_off + kTmemO + (uint32_t)(tl * kBM + ch * 64 + h * 32), o);
+                    ptx::tmem_wait_ld();
+                    ptx::tmem_reg_fence(o);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) o[q] = 0u;   // every tile of the item was skipped
+                }
                 float4* d4 = reinterpret_cast<float4*>(dst + h * 32);
 #pragma unroll
                 for (int q = 0; q < 8; ++q)
@@ -429,7 +449,7 @@ __device__ void tp_epilogue(const TpParams& p, TpBarriers& bars, const uint8_t* 
         ptx::tc_fence_before();
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(&bars.o_empty);
-        gt += T;
+        gt += t;
     }
     if (!ok) record_error(p.err, DEV_TIMEOUT);
 }
@@ -576,7 +596,7 @@ size_t tp_partial_floats(const TcPlan& p) { return (size_t)p.n_split * p.rv * p.
 
 int launch_kmvm_tp(Ctx* ctx, const TcPlan& plan, const OperandLayout& L, const MvmArgs& a, const CUtensorMap& tmA,
                    const CUtensorMap& tmB, const CUtensorMap& tmV, const float* outscale, float* partial,
-                   cudaStream_t s) {
+                   const uint32_t* mask, cudaStream_t s) {
     TpParams prm;
     prm.n_ip = plan.n_it;
     prm.n_jt = plan.n_jt;
@@ -592,6 +612,8 @@ int launch_kmvm_tp(Ctx* ctx, const TcPlan& plan, const OperandLayout& L, const M
     prm.diag = a.diag_coef != 0.0f ? 1 : 0;
     prm.ld_part = plan.Nr_pad;
     prm.partial = partial;
+    prm.mask = mask;
+    prm.mask_words = (plan.n_jt + 31) / 32;
     prm.err = ctx->dev_err;
     prm.limit_ns = kWaitLimitNs;
     const int bf = (L.prec == GP_PREC_BF16) ? 1 : 0;

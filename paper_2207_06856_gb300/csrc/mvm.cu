@@ -67,6 +67,12 @@ static void kop_layout(A& a, KOp& op, int64_t Nr, int64_t Nc, int R_max, bool sq
         a.template take<unsigned>(128);
         a.template take<float>(op.tp.engine == 1 ? tp_partial_floats(op.tp)
                                                   : (size_t)op.tp.n_split * rp * op.tp.Nr_pad);
+        if (op.skip) {
+            a.template take<uint32_t>(skip_words(op.tp));
+            a.template take<float>((size_t)((Nr + 127) / 128) * 2 * op.d);
+            a.template take<float>((size_t)op.tp.n_jt * 2 * op.d);
+            a.template take<unsigned long long>(1);
+        }
     }
 }
 
@@ -74,7 +80,8 @@ int check_mvm_flags(int flags, bool allow_noise) {
     const int prec = flags & 0xff;
     if (prec != GP_PREC_FP32 && prec != GP_PREC_FP16 && prec != GP_PREC_BF16) return GP_ERR_INVALID;
     const int known = 0xff | GP_MVM_ADD_NOISE | GP_MVM_XSPLIT | GP_MVM_NO_XSPLIT | GP_MVM_SCALE_SQRT_N |
-                      GP_MVM_VSPLIT | GP_MVM_BF16_SINGLE | GP_MVM_ONE_TILE | GP_MVM_PSPLIT | GP_MVM_HALF_EXP;
+                      GP_MVM_VSPLIT | GP_MVM_BF16_SINGLE | GP_MVM_ONE_TILE | GP_MVM_PSPLIT | GP_MVM_HALF_EXP |
+                      GP_MVM_SKIP_TILES;
     if (flags & ~known) return GP_ERR_INVALID;
     if (!allow_noise && (flags & GP_MVM_ADD_NOISE)) return GP_ERR_INVALID;
     if ((flags & GP_MVM_XSPLIT) && (flags & GP_MVM_NO_XSPLIT)) return GP_ERR_INVALID;
@@ -92,6 +99,8 @@ static int kop_plan(const Ctx* ctx, KOp& op, const gp_hyp_t* hyp, int64_t Nr, in
     op.noise = (float)hyp->noise;
     op.R_max = R;
     if (op.prec == GP_PREC_FP32) {
+        // the FP32 engine has no kernel tile to round: these options do not apply
+        if (flags & (GP_MVM_SKIP_TILES | GP_MVM_HALF_EXP)) return GP_ERR_UNSUPPORTED;
         op.sp = simt_plan(ctx, Nr, Nc, hyp->d, R < 32 ? R : 32);
     } else if (op.prec == GP_PREC_FP16 || op.prec == GP_PREC_BF16) {
         const bool bf = op.prec == GP_PREC_BF16;
@@ -124,6 +133,10 @@ static int kop_plan(const Ctx* ctx, KOp& op, const gp_hyp_t* hyp, int64_t Nr, in
         }
         op.lay = make_layout(hyp->d, op.prec, xsplit, vsplit, psplit);
         if (op.lay.k_pad == 0) return GP_ERR_UNSUPPORTED;
+        if (flags & GP_MVM_SKIP_TILES) {
+            if (!pair) return GP_ERR_UNSUPPORTED;
+            op.skip = true;
+        }
         if (flags & GP_MVM_HALF_EXP) {
             if (bf || !pair || psplit || op.lay.k_pad != 16 || hyp->kernel != GP_KERNEL_RBF) return GP_ERR_UNSUPPORTED;
             op.lay.half_exp = 1;
@@ -172,6 +185,12 @@ int kop_prepare(Ctx* ctx, WsCarver& wc, KOp& op, const gp_hyp_t* hyp, const floa
     op.bbox = wc.take<unsigned>(128);
     op.partial = wc.take<float>(op.tp.engine == 1 ? tp_partial_floats(op.tp)
                                                   : (size_t)op.tp.n_split * rp * op.tp.Nr_pad);
+    if (op.skip) {
+        op.mask = wc.take<uint32_t>(skip_words(op.tp));
+        op.rbox = wc.take<float>((size_t)((Nr + 127) / 128) * 2 * op.d);
+        op.cbox = wc.take<float>((size_t)op.tp.n_jt * 2 * op.d);
+        op.skip_count = wc.take<unsigned long long>(1);
+    }
     if (!wc.ok) return GP_ERR_WORKSPACE;
     GPK_TRY(launch_bbox(ctx, Xc, Nc, hyp->d, op.bbox, s));
     if (square) {
@@ -188,6 +207,7 @@ int kop_prepare(Ctx* ctx, WsCarver& wc, KOp& op, const gp_hyp_t* hyp, const floa
                            swizzle_for_row_bytes(arb)));
     GPK_TRY(encode_tmap_2d(&op.tmB, dt, op.XB, op.lay.k_pad, op.tp.Nc_pad, rowb, arb / 2, 128,
                            swizzle_for_row_bytes(arb)));
+    if (op.skip) GPK_TRY(prepare_skip(ctx, op, s));
     return GP_OK;
 }
 
@@ -227,7 +247,8 @@ int kop_apply(Ctx* ctx, KOp& op, const float* V, int R, float* out, int64_t ld_o
                 // one box carries the hi and lo rows of a 64-column K-block
                 GPK_TRY(encode_tmap_2d(&op.tmV, dt, op.Vt, pl.Nc_pad, vrows, pl.Nc_pad * 2, 64, (uint32_t)pl.rv,
                                        CU_TENSOR_MAP_SWIZZLE_128B));
-                GPK_TRY(launch_kmvm_tp(ctx, pl, op.lay, a, op.tmA, op.tmB, op.tmV, op.outscale, op.partial, s));
+                GPK_TRY(launch_kmvm_tp(ctx, pl, op.lay, a, op.tmA, op.tmB, op.tmV, op.outscale, op.partial,
+                                       op.skip ? op.mask : nullptr, s));
             } else {
                 GPK_TRY(encode_tmap_2d(&op.tmV, dt, op.Vt, pl.Nc_pad, vrows, pl.Nc_pad * 2, 64, pl.R_pad,
                                        CU_TENSOR_MAP_SWIZZLE_128B));

@@ -47,6 +47,7 @@ MVM_BF16_SINGLE = 0x2000
 MVM_ONE_TILE = 0x4000
 MVM_PSPLIT = 0x8000
 MVM_HALF_EXP = 0x10000
+MVM_SKIP_TILES = 0x20000
 
 
 def _check_flags(check_precision, prec: int) -> int:
@@ -401,6 +402,30 @@ def cg_solve(ctx: Context, hyp: Hyper, X, B, precond: Precond | None = None, tol
             "alpha": al.reshape(max_iter, R)[:it], "beta": be.reshape(max_iter, R)[:it],
             "resid_hist": rh.reshape(max_iter + 1, R)[:it + 1], "lanczos_len": lz}
     return U, st, info
+
+
+def kmvm_tile_count(ctx: Context, hyp: Hyper, Xr, Xc=None, precision="fp16", flags=0, stream=None):
+    """gp_kmvm_tile_count: (evaluated, total) (row-tile pair, column tile) entries
+    of the MVM gp_kmvm runs with these flags (GP_MVM_SKIP_TILES skips the
+    entries whose kernel values all round to zero)."""
+    Xc = Xr if Xc is None else Xc
+    Nr, d = Xr.shape
+    Nc = Xc.shape[0]
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    fl = prec | int(flags)
+    need = kmvm_workspace_size(hyp, Nr, Nc, 1, fl)
+    if need > ctx.workspace_bytes:
+        ctx.reserve(need)
+    fn = lib().gp_kmvm_tile_count
+    fn.restype = _c_int
+    fn.argtypes = [_c_void_p, ctypes.POINTER(_Hyp), _c_void_p, _c_i64, _c_void_p, _c_i64, _c_int,
+                   ctypes.POINTER(_c_i64), ctypes.POINTER(_c_i64), _c_void_p]
+    ev, tot = _c_i64(0), _c_i64(0)
+    h = hyp.c()
+    st = fn(ctx.ptr, ctypes.byref(h), _dev_ptr(Xr, "Xr", (Nr, d)), Nr, _dev_ptr(Xc, "Xc", (Nc, d)), Nc, fl,
+            ctypes.byref(ev), ctypes.byref(tot), _stream_ptr(stream))
+    _check(st, "gp_kmvm_tile_count")
+    return int(ev.value), int(tot.value)
 
 
 def kmvm_noalloc(hyp: Hyper, Xr, V, Xc=None, precision="fp16", add_noise=False, flags=0, out=None, stream=None):

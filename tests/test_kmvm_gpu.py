@@ -324,3 +324,65 @@ def test_kmvm_nonfinite_input_is_reported(ctx, where):
         ctx.check()
     assert ei.value.status == gpk.GP_ERR_NONFINITE
     ctx.check()   # the word was cleared
+
+
+def _clusters(n_per, centres, spread, seed, ragged=0):
+    """Points in tight clusters, written cluster by cluster (so 128-row tiles
+    are compact), with the last `ragged` points dropped."""
+    rng = np.random.default_rng(seed)
+    X = np.concatenate([c + spread * rng.standard_normal((n_per, len(c))) for c in centres])
+    return X[:len(X) - ragged].astype(np.float32)
+
+
+@pytest.mark.parametrize("prec,flags_name,kern", [("fp16", "", 0), ("fp16", "", 1), ("fp16", "MVM_PSPLIT", 0),
+                                                  ("fp16", "MVM_HALF_EXP", 0), ("bf16", "", 0), ("fp16", "", 3)])
+def test_skip_tiles_bit_identical_clustered(ctx, prec, flags_name, kern):
+    """Compact support (Sec. 3.1, Fig. 2c): 16 clusters 40 lengthscales apart
+    (within +-90 lengthscales of the origin, where the FP16 norm terms fit),
+    stored cluster by cluster, plus a pair of clusters just beyond the FP16
+    underflow distance of the RBF kernel (6.3 lengthscales, the adversarial
+    case for the margin).  Skipping the tiles whose kernel values all round to
+    zero leaves the result bit-identical, while most entries are skipped."""
+    from paper_2207_06856_gb300 import gpk
+    d = 3
+    g = (np.arange(4) - 1.5) * 40.0
+    centres = [np.array([a, b, 0.0]) for a in g for b in g] + [np.array([0.0, 90.0, 0]), np.array([6.3, 90.0, 0])]
+    X = _clusters(700, centres, 0.05, seed=44, ragged=37)
+    N = X.shape[0]
+    V = np.random.default_rng(45).standard_normal((17, N)).astype(np.float32)
+    ls = np.ones(d, np.float32)
+    base = getattr(gpk, flags_name) if flags_name else 0
+    a = _run(ctx, X, V, kern, ls, 1.0, 0.05, prec, flags=base)
+    b = _run(ctx, X, V, kern, ls, 1.0, 0.05, prec, flags=base | gpk.MVM_SKIP_TILES)
+    assert np.array_equal(a, b)
+    hyp = gpk.Hyper(kern, ls, 1.0, 0.05)
+    ev, tot = gpk.kmvm_tile_count(ctx, hyp, torch.from_numpy(X).to("cuda:0"), precision=prec,
+                                  flags=base | gpk.MVM_SKIP_TILES)
+    assert ev < 0.35 * tot, (ev, tot)
+
+
+def test_skip_tiles_bit_identical_precision_workload(ctx):
+    """The benchmark's MVM (N = 65,536, d = 8 standard normal, l = 1): the bound
+    skips nothing there (the data has no far-apart tiles) and the result is
+    bit-identical."""
+    from paper_2207_06856_gb300 import gpk
+    w = workloads.precision()
+    dev = torch.device("cuda:0")
+    hyp = gpk.Hyper(w.kernel, w.lengthscale, w.outputscale, w.noise)
+    X = torch.from_numpy(w.X).to(dev)
+    B = torch.from_numpy(w.rhs()).to(dev)
+    a = gpk.kmvm(ctx, hyp, X, B, precision="fp16", add_noise=True).cpu().numpy()
+    b = gpk.kmvm(ctx, hyp, X, B, precision="fp16", add_noise=True, flags=gpk.MVM_SKIP_TILES).cpu().numpy()
+    ctx.check()
+    assert np.array_equal(a, b)
+    ev, tot = gpk.kmvm_tile_count(ctx, hyp, X, flags=gpk.MVM_SKIP_TILES)
+    assert 0 < ev <= tot
+
+
+@pytest.mark.parametrize("case", ["fp32", "one_tile"])
+def test_skip_tiles_unsupported(ctx, case):
+    from paper_2207_06856_gb300 import gpk
+    X, V, kern, ls, a2, s2 = workloads.random_problem(300, 3, 2, seed=46)
+    prec, fl = ("fp32", gpk.MVM_SKIP_TILES) if case == "fp32" else ("fp16", gpk.MVM_SKIP_TILES | gpk.MVM_ONE_TILE)
+    with pytest.raises(gpk.GPKError):
+        _run(ctx, X, V, kern, ls, a2, s2, prec, flags=fl)
