@@ -455,6 +455,47 @@ def run_kmvm(args):
                       "avg_launch_ms": ms / max(n, 1), "pairs_per_s": pairs / (ms / max(n, 1) / 1e3)}), flush=True)
 
 
+def run_sumstudy(args):
+    """Summation-variant study (Sec. 4.1, Fig. 4b; App. B, Fig. A.1a) on inputs
+    shaped like the scale workload (N = 65,536 drawn from its distribution,
+    d = 11, Matern-3/2 ARD), one right-hand side y: the CUDA-core FP16 MVM with
+    each accumulation scheme and the tensor-core FP16 MVM, time and relative
+    error on 512 sampled rows against the FP64 oracle."""
+    import torch
+    import oracle as O
+    from oracle import cfp64 as C
+    from paper_2207_06856_gb300 import gpk, workloads
+    w = workloads.scale(N=args.study_n)
+    N = w.X.shape[0]
+    ctx = gpk.Context(0)
+    hyp = gpk.Hyper(w.kernel, w.lengthscale, w.outputscale, w.noise)
+    X = torch.from_numpy(w.X).cuda()
+    V = torch.from_numpy(w.y[None, :].astype(np.float32)).cuda()
+    rows = np.sort(np.random.default_rng(4).choice(N, 512, replace=False))
+    oh = O.Hyp(workloads.KERNEL_NAMES[w.kernel], w.lengthscale.astype(np.float64), w.outputscale, w.noise)
+    ref = C.kmvm(w.X, w.y.astype(np.float64)[:, None], oh, rows=rows)[:, 0]
+    res = {}
+    names = {0: "tensor_core_fp32_acc", 1: "simt_fp16_fp32_acc", 2: "simt_fp16_half_acc",
+             3: "simt_fp16_block_sums", 4: "simt_fp16_kahan"}
+    for s_ in (0, 1, 2, 3, 4):
+        fl = gpk.MVM_SUM(s_) if s_ else 0
+        out = gpk.kmvm(ctx, hyp, X, V, precision="fp16", add_noise=True, flags=fl)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            gpk.kmvm(ctx, hyp, X, V, precision="fp16", add_noise=True, flags=fl, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        got = out[0].cpu().numpy().astype(np.float64)[rows]
+        res[names[s_]] = {"ms": e0.elapsed_time(e1) / args.steps,
+                          "rel_err": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
+    ctx.check()
+    print(json.dumps({"mode": "sumstudy", "N": N, "d": int(w.X.shape[1]), "kernel": "matern32", "R": 1,
+                      "variants": res}), flush=True)
+
+
 def run_vjp(args):
     """The backward of the kernel MVM alone on the differentiation workload
     (N = 262,144, d = 18, ARD RBF, 17 columns): the tensor-core FP16 backward
@@ -716,12 +757,13 @@ def main():
     ap.add_argument("--extra-diff-steps", type=int, default=4)
     ap.add_argument("--extra-serve-requests", type=int, default=96)
     ap.add_argument("--ref-iters", type=int, default=152)
-    ap.add_argument("--mode", default="solve", choices=["solve", "kmvm", "serve", "diff", "scale", "vjp"])
+    ap.add_argument("--mode", default="solve", choices=["solve", "kmvm", "serve", "diff", "scale", "vjp", "sumstudy"])
     ap.add_argument("--diff-steps", type=int, default=20)
     ap.add_argument("--diff-n", type=int, default=262144)
     ap.add_argument("--diff-tol", type=float, default=1.0)
     ap.add_argument("--diff-max-iter", type=int, default=50)
     ap.add_argument("--scale-n", type=int, default=1843200)
+    ap.add_argument("--study-n", type=int, default=65536)
     ap.add_argument("--one-tile", action="store_true", help="kmvm mode: the one-row-tile tensor-core engine")
     ap.add_argument("--psplit", action="store_true", help="kmvm mode: FP16 kernel tile as hi + lo")
     ap.add_argument("--half-exp", action="store_true", help="kmvm mode: FP16 exp2 argument and exponential")
@@ -743,6 +785,8 @@ def main():
         run_scale(args)
     elif args.mode == "vjp":
         run_vjp(args)
+    elif args.mode == "sumstudy":
+        run_sumstudy(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -99,6 +99,13 @@ extern "C" {
                                        subnormal of the kernel tile's format, where
                                        it rounds to an exact 0 (bit-identical
                                        result); pair engine, FP16 / BF16            */
+/* Summation-variant study (Sec. 4.1, Fig. 4b; App. B, Fig. A.1a), FP16 only, R <= 8:
+ * a CUDA-core FP16 MVM (kernel value and products in FP16) whose row sums are
+ * accumulated by scheme x: 1 FP32, 2 FP16 (one running sum), 3 FP16 per
+ * 128-column block then FP32 across blocks, 4 Kahan-compensated FP16.  A study
+ * engine, not the hot path.                                                    */
+#define GP_MVM_SUM(x)     (((x) & 0x7) << 18)
+#define GP_MVM_SUM_MASK   (0x7 << 18)
 #define GP_MVM_ONE_TILE     0x4000  /* tensor-core MVM on the one-row-tile engine
                                        (P V with M = 128 rows, N = R) instead of
                                        the default pair engine (transposed

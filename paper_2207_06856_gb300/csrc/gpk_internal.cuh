@@ -163,6 +163,11 @@ size_t simt_partial_floats(const SimtPlan& p, int64_t Nr);
 int launch_kmvm_simt(Ctx* ctx, const SimtPlan& plan, const MvmArgs& a, float outputscale, const float* Xrs,
                      const float* Xcs, const float* V, float* partial, cudaStream_t s);
 
+// Summation-variant study engine (kmvm_sum.cu): CUDA-core FP16 products,
+// accumulation scheme 1..4 (GP_MVM_SUM), R <= 8, scaled inputs as the SIMT engine's.
+int launch_kmvm_sum(Ctx* ctx, int scheme, const MvmArgs& a, float outputscale, const float* Xrs, const float* Xcs,
+                    int dp, const float* V, const unsigned* cmax_bits, cudaStream_t s);
+
 // out[c][i] = scale_c * sum_s partial[s][c][i] + noise * Vnoise[c][i], with
 // partial laid out [n_split][RP][ld_part]; scale_c = outscale[c] or outscale_const.
 int launch_split_reduce(Ctx* ctx, const float* partial, int n_split, int64_t ld_part, int64_t Nr, int R, int RP,
@@ -189,6 +194,7 @@ struct KOp {
     unsigned* bbox = nullptr;
     float* partial = nullptr;
     CUtensorMap tmA, tmB, tmV;
+    int sum = 0;   // summation-variant study scheme (GP_MVM_SUM), 0 = none
     // compact-support tile skipping (GP_MVM_SKIP_TILES, pair engine)
     bool skip = false;
     uint32_t* mask = nullptr;

@@ -53,7 +53,11 @@ int encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, u
 // two can never disagree.
 template <class A>
 static void kop_layout(A& a, KOp& op, int64_t Nr, int64_t Nc, int R_max, bool square) {
-    if (op.prec == GP_PREC_FP32) {
+    if (op.sum) {
+        a.template take<float>((size_t)Nr * op.sp.dp);
+        if (!square) a.template take<float>((size_t)Nc * op.sp.dp);
+        a.template take<unsigned>(64);
+    } else if (op.prec == GP_PREC_FP32) {
         a.template take<float>((size_t)Nr * op.sp.dp);
         if (!square) a.template take<float>((size_t)Nc * op.sp.dp);
         a.template take<float>(simt_partial_floats(op.sp, Nr));
@@ -81,7 +85,9 @@ int check_mvm_flags(int flags, bool allow_noise) {
     if (prec != GP_PREC_FP32 && prec != GP_PREC_FP16 && prec != GP_PREC_BF16) return GP_ERR_INVALID;
     const int known = 0xff | GP_MVM_ADD_NOISE | GP_MVM_XSPLIT | GP_MVM_NO_XSPLIT | GP_MVM_SCALE_SQRT_N |
                       GP_MVM_VSPLIT | GP_MVM_BF16_SINGLE | GP_MVM_ONE_TILE | GP_MVM_PSPLIT | GP_MVM_HALF_EXP |
-                      GP_MVM_SKIP_TILES;
+                      GP_MVM_SKIP_TILES | GP_MVM_SUM_MASK;
+    const int sum = (flags & GP_MVM_SUM_MASK) >> 18;
+    if (sum > 4 || (sum && prec != GP_PREC_FP16)) return GP_ERR_INVALID;
     if (flags & ~known) return GP_ERR_INVALID;
     if (!allow_noise && (flags & GP_MVM_ADD_NOISE)) return GP_ERR_INVALID;
     if ((flags & GP_MVM_XSPLIT) && (flags & GP_MVM_NO_XSPLIT)) return GP_ERR_INVALID;
@@ -98,7 +104,14 @@ static int kop_plan(const Ctx* ctx, KOp& op, const gp_hyp_t* hyp, int64_t Nr, in
     op.a2 = (float)hyp->outputscale;
     op.noise = (float)hyp->noise;
     op.R_max = R;
-    if (op.prec == GP_PREC_FP32) {
+    op.sum = (flags & GP_MVM_SUM_MASK) >> 18;
+    if (op.sum) {
+        // summation-variant study: the CUDA-core FP16 engine on the SIMT engine's scaled inputs
+        if (R > 8 || (flags & (GP_MVM_SKIP_TILES | GP_MVM_HALF_EXP | GP_MVM_PSPLIT | GP_MVM_ONE_TILE)))
+            return GP_ERR_UNSUPPORTED;
+        op.sp = simt_plan(ctx, Nr, Nc, hyp->d, R);
+        if (op.sp.dp > 32) return GP_ERR_UNSUPPORTED;
+    } else if (op.prec == GP_PREC_FP32) {
         // the FP32 engine has no kernel tile to round: these options do not apply
         if (flags & (GP_MVM_SKIP_TILES | GP_MVM_HALF_EXP)) return GP_ERR_UNSUPPORTED;
         op.sp = simt_plan(ctx, Nr, Nc, hyp->d, R < 32 ? R : 32);
@@ -164,6 +177,16 @@ int kop_prepare(Ctx* ctx, WsCarver& wc, KOp& op, const gp_hyp_t* hyp, const floa
     ScaleVec inv;
     memset(&inv, 0, sizeof(inv));
     const float c = kernel_input_scale(hyp->kernel);
+    if (op.sum) {
+        for (int k = 0; k < hyp->d; ++k) inv.v[k] = (float)((double)c / sqrt(2.0) / (double)hyp->lengthscale[k]);
+        op.Xs_r = wc.take<float>((size_t)Nr * op.sp.dp);
+        op.Xs_c = square ? op.Xs_r : wc.take<float>((size_t)Nc * op.sp.dp);
+        op.cmax = wc.take<unsigned>(64);
+        if (!wc.ok) return GP_ERR_WORKSPACE;
+        GPK_TRY(launch_prep_x_f32(ctx, Xr, Nr, Nr, hyp->d, op.sp.dp, inv, op.Xs_r, s));
+        if (!square) GPK_TRY(launch_prep_x_f32(ctx, Xc, Nc, Nc, hyp->d, op.sp.dp, inv, op.Xs_c, s));
+        return GP_OK;
+    }
     if (op.prec == GP_PREC_FP32) {
         // SIMT engine: q = |x^_i - x^_j|^2 with x^ = (c / sqrt2) x / l, so s = -q.
         for (int k = 0; k < hyp->d; ++k) inv.v[k] = (float)((double)c / sqrt(2.0) / (double)hyp->lengthscale[k]);
@@ -229,7 +252,10 @@ int kop_apply(Ctx* ctx, KOp& op, const float* V, int R, float* out, int64_t ld_o
         // on-chip distance would show; its diagonal is added exactly instead.
         a.diag_coef = (op.square && op.prec != GP_PREC_FP32 && op.kernel == GP_KERNEL_MATERN12) ? op.a2 : 0.0f;
         const float* Vc = V + (int64_t)c0 * op.Nc;
-        if (op.prec == GP_PREC_FP32) {
+        if (op.sum) {
+            GPK_TRY(launch_v_colmax(ctx, Vc, op.Nc, rc, op.cmax, s));
+            GPK_TRY(launch_kmvm_sum(ctx, op.sum, a, op.a2, op.Xs_r, op.Xs_c, op.sp.dp, Vc, op.cmax, s));
+        } else if (op.prec == GP_PREC_FP32) {
             SimtPlan pl = op.sp;
             pl.R_pad = ((rc + 3) / 4) * 4;   // <= the plan's, which sized the partial buffer
             GPK_TRY(launch_kmvm_simt(ctx, pl, a, op.a2, op.Xs_r, op.Xs_c, Vc, op.partial, s));

@@ -50,6 +50,11 @@ MVM_HALF_EXP = 0x10000
 MVM_SKIP_TILES = 0x20000
 
 
+def MVM_SUM(scheme: int) -> int:
+    """Summation-variant study flag: 1 FP32, 2 FP16, 3 FP16 block sums, 4 Kahan FP16."""
+    return (int(scheme) & 0x7) << 18
+
+
 def _check_flags(check_precision, prec: int) -> int:
     return PRECISIONS[check_precision] if isinstance(check_precision, str) else int(check_precision)
 

@@ -386,3 +386,33 @@ def test_skip_tiles_unsupported(ctx, case):
     prec, fl = ("fp32", gpk.MVM_SKIP_TILES) if case == "fp32" else ("fp16", gpk.MVM_SKIP_TILES | gpk.MVM_ONE_TILE)
     with pytest.raises(gpk.GPKError):
         _run(ctx, X, V, kern, ls, a2, s2, prec, flags=fl)
+
+
+def test_summation_variants_ordering(ctx):
+    """Summation-variant study (Sec. 4.1, Fig. 4b; App. B, Fig. A.1a) on inputs
+    shaped like the scale workload (d = 11, Matern-3/2, anisotropic mixture):
+    with FP16 kernel values and FP16 products, accumulating in FP32 meets the
+    FP16 MVM tolerance; one running FP16 sum is far worse; FP16 block sums and
+    Kahan-compensated FP16 sums recover most of the loss."""
+    from paper_2207_06856_gb300 import gpk
+    w = workloads.scale(N=6000)
+    X = w.X
+    V = np.stack([w.y, np.random.default_rng(47).standard_normal(X.shape[0])]).astype(np.float32)
+    ls = w.lengthscale
+    ref = _ref(X, V, w.kernel, ls, w.outputscale, w.noise)
+    err = {}
+    for s in (1, 2, 3, 4):
+        got = _run(ctx, X, V, w.kernel, ls, w.outputscale, w.noise, "fp16", flags=gpk.MVM_SUM(s))
+        err[s] = _colerr(got, ref)
+    assert err[1] <= TOL["fp16"], err
+    assert err[2] > 3 * err[1], err
+    assert err[3] < err[2] and err[4] < err[2], err
+
+
+def test_summation_variants_refuse_other_shapes(ctx):
+    from paper_2207_06856_gb300 import gpk
+    X, V, kern, ls, a2, s2 = workloads.random_problem(300, 3, 9, seed=48)
+    with pytest.raises(gpk.GPKError):     # more than 8 right-hand sides
+        _run(ctx, X, V, kern, ls, a2, s2, "fp16", flags=gpk.MVM_SUM(2))
+    with pytest.raises(gpk.GPKError):     # FP16 only
+        _run(ctx, X, V[:2], kern, ls, a2, s2, "bf16", flags=gpk.MVM_SUM(2))
