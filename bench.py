@@ -357,7 +357,7 @@ def run_ours(args):
         d = diff_measure(args, args.extra_diff_steps)
         extras["differentiation"] = {k: d[k] for k in ("value", "unit", "steps", "config", "loss_first", "loss_last",
                                                        "subsample_exact_nll_initial", "subsample_exact_nll_final",
-                                                       "cg_iters", "clocks")}
+                                                       "cg_iters", "backward", "clocks")}
         sc = scale_measure(args)
         extras["scale"] = {k: sc[k] for k in ("value", "unit", "config", "mll", "cg_iters", "rel_resid_y_reported",
                                               "rel_resid_y_fp64_sampled_512_rows", "pairs_per_mvm", "clocks")}
@@ -496,41 +496,57 @@ def run_sumstudy(args):
                       "variants": res}), flush=True)
 
 
-def run_vjp(args):
-    """The backward of the kernel MVM alone on the differentiation workload
-    (N = 262,144, d = 18, ARD RBF, 17 columns): the tensor-core FP16 backward
-    and the CUDA-core FP32 one, CUDA-event timed; pairs/s = N^2 / time."""
+def vjp_timing(ctx, w, steps: int, precisions=("fp16", "fp32")) -> dict:
+    """CUDA-event time of the MVM backward on workload w (17 columns, gradient in
+    X too), per precision, with pairs/s = N^2 / time."""
     import torch
-    from paper_2207_06856_gb300 import gpk, workloads
-    w = workloads.differentiation(N=args.diff_n)
+    from paper_2207_06856_gb300 import gpk
     N = w.X.shape[0]
-    ctx = gpk.Context(0)
     hyp = gpk.Hyper(w.kernel, w.lengthscale, w.outputscale, w.noise)
     X = torch.from_numpy(w.X).cuda()
     rng = np.random.default_rng(5)
     U = torch.from_numpy(rng.standard_normal((17, N)).astype(np.float32)).cuda()
     W = torch.from_numpy(rng.standard_normal((17, N)).astype(np.float32)).cuda()
     res = {}
-    for prec in ("fp16", "fp32"):
+    for prec in precisions:
         for _ in range(2):
             gpk.kmvm_vjp(ctx, hyp, X, U, W, want_X=True, precision=prec)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(args.steps):
+        for _ in range(steps):
             gpk.kmvm_vjp(ctx, hyp, X, U, W, want_X=True, precision=prec)
         e1.record()
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
+        ms = e0.elapsed_time(e1) / steps
         res[prec] = {"ms_per_backward": ms, "pairs_per_s": float(N) ** 2 / (ms * 1e-3)}
-    ctx.profile(True)
-    gpk.kmvm_vjp(ctx, hyp, X, U, W, want_X=True, precision="fp16")
-    kms, kn = ctx.profile_read()
-    ctx.profile(False)
-    res["fp16"]["kernel_ms"] = kms / max(kn, 1)
+    if "fp16" in precisions:
+        ctx.profile(True)
+        gpk.kmvm_vjp(ctx, hyp, X, U, W, want_X=True, precision="fp16")
+        kms, kn = ctx.profile_read()
+        ctx.profile(False)
+        peaks = ctx.measure_peaks()
+        kpairs = float(N) ** 2 / (kms / max(kn, 1) * 1e-3)
+        res["fp16"].update({"kernel_ms": kms / max(kn, 1), "kernel_pairs_per_s": kpairs,
+                            "roofline": {"bound": "alu", "achieved": kpairs / 1e9, "peak": peaks["ex2_per_s"] / 1e9,
+                                         "unit": "Gpairs/s", "frac": kpairs / peaks["ex2_per_s"],
+                                         "peak_source": "measured ex2 rate on this GPU, one ex2 per pair (RBF)",
+                                         "kernel": "kvjp_tc_kernel"}})
     ctx.check()
-    print(json.dumps({"mode": "vjp", "N": N, "d": int(w.X.shape[1]), "R": 17, **res}), flush=True)
+    return res
+
+
+def run_vjp(args):
+    """The backward of the kernel MVM alone on the differentiation workload
+    (N = 262,144, d = 18, ARD RBF, 17 columns): the tensor-core FP16 backward
+    and the CUDA-core FP32 one, CUDA-event timed; pairs/s = N^2 / time."""
+    from paper_2207_06856_gb300 import gpk, workloads
+    w = workloads.differentiation(N=args.diff_n)
+    ctx = gpk.Context(0)
+    precs = ("fp16",) if args.vjp_fp16_only else ("fp16", "fp32")
+    res = vjp_timing(ctx, w, args.steps, precs)
+    print(json.dumps({"mode": "vjp", "N": int(w.X.shape[0]), "d": int(w.X.shape[1]), "R": 17, **res}), flush=True)
 
 
 def run_serve(args):
@@ -674,6 +690,7 @@ def diff_measure(args, n_steps):
         "lengthscale_last": [float(v) for v in hist[-1][1]], "outputscale_last": hist[-1][2],
         "noise_last": hist[-1][3], "cg_iters": iters, "total_s": float(np.sum(step_s)),
         "gpu_launches": int(ctx.launches - launches0), "clocks": clocks,
+        "backward": vjp_timing(ctx, w, 3, ("fp16",)),
     }
     ctx.close()
     return line
@@ -764,6 +781,7 @@ def main():
     ap.add_argument("--diff-max-iter", type=int, default=50)
     ap.add_argument("--scale-n", type=int, default=1843200)
     ap.add_argument("--study-n", type=int, default=65536)
+    ap.add_argument("--vjp-fp16-only", action="store_true")
     ap.add_argument("--one-tile", action="store_true", help="kmvm mode: the one-row-tile tensor-core engine")
     ap.add_argument("--psplit", action="store_true", help="kmvm mode: FP16 kernel tile as hi + lo")
     ap.add_argument("--half-exp", action="store_true", help="kmvm mode: FP16 exp2 argument and exponential")
