@@ -416,10 +416,11 @@ def run_kmvm(args):
     hyp = gpk.Hyper(w.kernel, w.lengthscale, w.outputscale, w.noise)
     ctx = gpk.Context(0)
     X = torch.from_numpy(w.X).cuda()
-    B = torch.from_numpy(w.rhs()).cuda()
+    B = torch.from_numpy(w.rhs()[:args.nrhs] if args.nrhs else w.rhs()).cuda().contiguous()
     out = torch.empty_like(B)
     fl = (gpk.MVM_ONE_TILE if args.one_tile else 0) | (gpk.MVM_PSPLIT if args.psplit else 0) | \
-        (gpk.MVM_HALF_EXP if args.half_exp else 0) | (gpk.MVM_SKIP_TILES if args.skip_tiles else 0)
+        (gpk.MVM_HALF_EXP if args.half_exp else 0) | (gpk.MVM_SKIP_TILES if args.skip_tiles else 0) | \
+        (gpk.MVM_SYMMETRIC if args.symmetric else 0)
     if args.clustered:
         # compact-support case: 16 clusters of 4,096 points (d = 8, within-cluster std 0.3 lengthscales,
         # centres 20 lengthscales apart), stored cluster by cluster
@@ -444,10 +445,11 @@ def run_kmvm(args):
     ctx.check()
     pairs = float(w.N) ** 2
     ev, tot = gpk.kmvm_tile_count(ctx, hyp, X, precision=args.precision, flags=fl) if args.precision != "fp32" \
-        else (1, 1)
-    print(json.dumps({"mode": "kmvm", "precision": args.precision, "kernel": args.kernel,
+        else ((w.N + 1, 2 * w.N) if args.symmetric else (1, 1))   # symmetric: N (N + 1) / 2 of N^2 pairs
+    print(json.dumps({"mode": "kmvm", "precision": args.precision, "kernel": args.kernel, "rhs": int(B.shape[0]),
                       "inputs": "clustered (16 clusters)" if args.clustered else "precision workload",
-                      "skip_tiles": bool(args.skip_tiles), "evaluated_fraction": ev / tot,
+                      "skip_tiles": bool(args.skip_tiles), "symmetric": bool(args.symmetric),
+                      "evaluated_fraction": ev / tot,
                       "evaluated_pairs_per_s": pairs * ev / tot / (ms / max(n, 1) / 1e3),
                       "engine": "one-tile" if args.one_tile else "pair", "psplit": bool(args.psplit),
                       "half_exp": bool(args.half_exp),
@@ -787,6 +789,8 @@ def main():
     ap.add_argument("--half-exp", action="store_true", help="kmvm mode: FP16 exp2 argument and exponential")
     ap.add_argument("--skip-tiles", action="store_true", help="kmvm mode: compact-support tile skipping")
     ap.add_argument("--clustered", action="store_true", help="kmvm mode: clustered inputs (16 far-apart clusters)")
+    ap.add_argument("--symmetric", action="store_true", help="kmvm mode: FP32 symmetric half-work MVM")
+    ap.add_argument("--nrhs", type=int, default=0, help="kmvm mode: use the first NRHS right-hand sides (0: all 17)")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-arena-gb", type=float, default=48.0)

@@ -106,6 +106,16 @@ extern "C" {
  * engine, not the hot path.                                                    */
 #define GP_MVM_SUM(x)     (((x) & 0x7) << 18)
 #define GP_MVM_SUM_MASK   (0x7 << 18)
+#define GP_MVM_SYMMETRIC 0x200000  /* FP32 only, square operator (Xc == Xr),
+                                       R <= 24, d <= 32: K = K^T, each kernel value
+                                       evaluated once for the row and the column
+                                       it belongs to (N(N+1)/2 evaluations; an
+                                       extension toward the Conclusion's future
+                                       work); sums added with FP32 atomics, so the
+                                       last bits vary from run to run.  Other
+                                       shapes: GP_ERR_UNSUPPORTED (non-square,
+                                       R > 24, d > 32) or GP_ERR_INVALID (with a
+                                       non-FP32 precision). */
 #define GP_MVM_ONE_TILE     0x4000  /* tensor-core MVM on the one-row-tile engine
                                        (P V with M = 128 rows, N = R) instead of
                                        the default pair engine (transposed
@@ -135,6 +145,17 @@ GPK_API size_t gp_ctx_workspace_bytes(const gp_ctx* ctx);
 /* Synchronise `stream`, read and clear the device error word; returns
  * GP_ERR_TIMEOUT (or another GP_ERR_*) if a kernel recorded one. */
 GPK_API int gp_ctx_check(gp_ctx* ctx, void* stream);
+/* Failure-detection check of the device-side bounded waits: launches one warp
+ * that waits on an mbarrier nothing completes, with the wait helper of the MVM
+ * kernels (sleep = 0: spinning try_wait, 1: try_wait with a suspend hint) and
+ * a limit of `limit_ms` (0 < limit_ms <= 1000).  The wait gives up, the kernel
+ * records a timeout in the context's device error word and returns, so the
+ * next gp_ctx_check on the stream returns GP_ERR_TIMEOUT and the context stays
+ * usable.  If `waited_cycles` is not null, the SM clock cycles the wait lasted
+ * are written there (the call then synchronises the stream and uses the first
+ * 8 bytes of the workspace).  Errors: GP_ERR_INVALID, GP_ERR_WORKSPACE,
+ * GP_ERR_CUDA. */
+GPK_API int gp_wait_check(gp_ctx* ctx, double limit_ms, int sleep, long long* waited_cycles, void* stream);
 /* Number of kernels this context has launched since creation (all entry
  * points; each CUDA kernel launch counts one). */
 GPK_API int64_t gp_ctx_launch_count(const gp_ctx* ctx);

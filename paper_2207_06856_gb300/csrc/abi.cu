@@ -1,5 +1,6 @@
 // C ABI: context management, status strings, argument validation and gp_kmvm.
 #include "gpk_internal.cuh"
+#include "ptx.cuh"
 
 #include <math.h>
 #include <new>
@@ -23,6 +24,26 @@ struct DeviceGuard {
         if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
     }
 };
+
+// The bounded-wait path of the kernels, exercised on a wait that nothing
+// completes: an mbarrier expecting one arrival that never comes.  Every lane
+// waits with the helper the MVM kernels use (spin or hinted), gives up after
+// the limit and lane 0 records DEV_TIMEOUT in the error word.
+__global__ void wait_check_kernel(uint64_t limit_ns, int sleep, int* err, long long* waited_cycles) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        ptx::mbar_init(&bar, 1);
+        ptx::fence_mbar_init();
+    }
+    __syncwarp();
+    const long long t0 = clock64();
+    const bool ok = sleep ? ptx::mbar_wait_sleep(&bar, 0, limit_ns) : ptx::mbar_wait(&bar, 0, limit_ns);
+    const long long t1 = clock64();
+    if (threadIdx.x == 0) {
+        if (!ok) atomicCAS(err, DEV_OK, DEV_TIMEOUT);
+        if (waited_cycles) *waited_cycles = t1 - t0;
+    }
+}
 
 }  // namespace
 
@@ -121,6 +142,26 @@ int gp_ctx_reserve(gp_ctx* ctx, size_t workspace_bytes) {
 size_t gp_ctx_workspace_bytes(const gp_ctx* ctx) { return ctx ? ctx->ws_bytes : 0; }
 
 int64_t gp_ctx_launch_count(const gp_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int gp_wait_check(gp_ctx* ctx, double limit_ms, int sleep, long long* waited_cycles, void* stream) {
+    if (!ctx || !(limit_ms > 0.0) || limit_ms > 1000.0) return GP_ERR_INVALID;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    long long* dw = nullptr;
+    if (waited_cycles) {
+        if (ctx->ws_bytes < 256) return GP_ERR_WORKSPACE;
+        dw = (long long*)ctx->ws;
+    }
+    wait_check_kernel<<<1, 32, 0, s>>>((uint64_t)(limit_ms * 1e6), sleep ? 1 : 0, ctx->dev_err, dw);
+    ctx->launches++;
+    if (cudaGetLastError() != cudaSuccess) return GP_ERR_CUDA;
+    if (waited_cycles) {
+        if (cudaMemcpyAsync(waited_cycles, dw, sizeof(long long), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return GP_ERR_CUDA;
+    }
+    return GP_OK;
+}
 
 int gp_ctx_check(gp_ctx* ctx, void* stream) {
     if (!ctx) return GP_ERR_INVALID;

@@ -163,6 +163,10 @@ size_t simt_partial_floats(const SimtPlan& p, int64_t Nr);
 int launch_kmvm_simt(Ctx* ctx, const SimtPlan& plan, const MvmArgs& a, float outputscale, const float* Xrs,
                      const float* Xcs, const float* V, float* partial, cudaStream_t s);
 
+// Symmetric half-work FP32 engine (kmvm_sym.cu): square operator, R <= 24.
+int launch_kmvm_sym(Ctx* ctx, const MvmArgs& a, float outputscale, const float* Xs, int dp, const float* V,
+                    cudaStream_t s);
+
 // Summation-variant study engine (kmvm_sum.cu): CUDA-core FP16 products,
 // accumulation scheme 1..4 (GP_MVM_SUM), R <= 8, scaled inputs as the SIMT engine's.
 int launch_kmvm_sum(Ctx* ctx, int scheme, const MvmArgs& a, float outputscale, const float* Xrs, const float* Xcs,
@@ -195,6 +199,7 @@ struct KOp {
     float* partial = nullptr;
     CUtensorMap tmA, tmB, tmV;
     int sum = 0;   // summation-variant study scheme (GP_MVM_SUM), 0 = none
+    bool sym = false;   // symmetric half-work FP32 MVM (GP_MVM_SYMMETRIC)
     // compact-support tile skipping (GP_MVM_SKIP_TILES, pair engine)
     bool skip = false;
     uint32_t* mask = nullptr;

@@ -85,7 +85,8 @@ int check_mvm_flags(int flags, bool allow_noise) {
     if (prec != GP_PREC_FP32 && prec != GP_PREC_FP16 && prec != GP_PREC_BF16) return GP_ERR_INVALID;
     const int known = 0xff | GP_MVM_ADD_NOISE | GP_MVM_XSPLIT | GP_MVM_NO_XSPLIT | GP_MVM_SCALE_SQRT_N |
                       GP_MVM_VSPLIT | GP_MVM_BF16_SINGLE | GP_MVM_ONE_TILE | GP_MVM_PSPLIT | GP_MVM_HALF_EXP |
-                      GP_MVM_SKIP_TILES | GP_MVM_SUM_MASK;
+                      GP_MVM_SKIP_TILES | GP_MVM_SUM_MASK | GP_MVM_SYMMETRIC;
+    if ((flags & GP_MVM_SYMMETRIC) && prec != GP_PREC_FP32) return GP_ERR_INVALID;
     const int sum = (flags & GP_MVM_SUM_MASK) >> 18;
     if (sum > 4 || (sum && prec != GP_PREC_FP16)) return GP_ERR_INVALID;
     if (flags & ~known) return GP_ERR_INVALID;
@@ -115,6 +116,10 @@ static int kop_plan(const Ctx* ctx, KOp& op, const gp_hyp_t* hyp, int64_t Nr, in
         // the FP32 engine has no kernel tile to round: these options do not apply
         if (flags & (GP_MVM_SKIP_TILES | GP_MVM_HALF_EXP)) return GP_ERR_UNSUPPORTED;
         op.sp = simt_plan(ctx, Nr, Nc, hyp->d, R < 32 ? R : 32);
+        if (flags & GP_MVM_SYMMETRIC) {
+            if (Nr != Nc || R > 24 || op.sp.dp > 32) return GP_ERR_UNSUPPORTED;
+            op.sym = true;
+        }
     } else if (op.prec == GP_PREC_FP16 || op.prec == GP_PREC_BF16) {
         const bool bf = op.prec == GP_PREC_BF16;
         // Inputs carried as hi + lo by default for BF16 (8-bit significand), for
@@ -255,6 +260,9 @@ int kop_apply(Ctx* ctx, KOp& op, const float* V, int R, float* out, int64_t ld_o
         if (op.sum) {
             GPK_TRY(launch_v_colmax(ctx, Vc, op.Nc, rc, op.cmax, s));
             GPK_TRY(launch_kmvm_sum(ctx, op.sum, a, op.a2, op.Xs_r, op.Xs_c, op.sp.dp, Vc, op.cmax, s));
+        } else if (op.sym) {
+            if (!op.square) return GP_ERR_UNSUPPORTED;
+            GPK_TRY(launch_kmvm_sym(ctx, a, op.a2, op.Xs_r, op.sp.dp, Vc, s));
         } else if (op.prec == GP_PREC_FP32) {
             SimtPlan pl = op.sp;
             pl.R_pad = ((rc + 3) / 4) * 4;   // <= the plan's, which sized the partial buffer

@@ -48,6 +48,7 @@ MVM_ONE_TILE = 0x4000
 MVM_PSPLIT = 0x8000
 MVM_HALF_EXP = 0x10000
 MVM_SKIP_TILES = 0x20000
+MVM_SYMMETRIC = 0x200000
 
 
 def MVM_SUM(scheme: int) -> int:
@@ -130,6 +131,7 @@ def _declare(lib):
         "gp_ctx_workspace_bytes": (_c_size, [_c_void_p]),
         "gp_ctx_check": (_c_int, [_c_void_p, _c_void_p]),
         "gp_ctx_launch_count": (_c_i64, [_c_void_p]),
+        "gp_wait_check": (_c_int, [_c_void_p, ctypes.c_double, _c_int, ctypes.POINTER(ctypes.c_longlong), _c_void_p]),
         "gp_kmvm_workspace_size": (_c_size, [ctypes.POINTER(_Hyp), _c_i64, _c_i64, _c_int, _c_int]),
         "gp_kmvm": (_c_int, [_c_void_p, ctypes.POINTER(_Hyp), _c_void_p, _c_i64, _c_void_p, _c_i64,
                              _c_void_p, _c_int, _c_void_p, _c_int, _c_void_p]),
@@ -269,6 +271,14 @@ class Context:
 
     def check(self, stream=None):
         _check(lib().gp_ctx_check(self._p, _c_void_p(_stream_ptr(stream))), "device error")
+
+    def wait_check(self, limit_ms: float, sleep: bool = False, stream=None) -> int:
+        """gp_wait_check: run a bounded device wait that nothing completes; the
+        timeout shows at the next check().  Returns the SM cycles it waited."""
+        cyc = ctypes.c_longlong(0)
+        _check(lib().gp_wait_check(self._p, float(limit_ms), 1 if sleep else 0, ctypes.byref(cyc),
+                                   _c_void_p(_stream_ptr(stream))), "gp_wait_check")
+        return int(cyc.value)
 
     def profile(self, enable: bool = True):
         """Record CUDA events around every tensor-core MVM launch."""

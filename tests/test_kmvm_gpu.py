@@ -416,3 +416,52 @@ def test_summation_variants_refuse_other_shapes(ctx):
         _run(ctx, X, V, kern, ls, a2, s2, "fp16", flags=gpk.MVM_SUM(2))
     with pytest.raises(gpk.GPKError):     # FP16 only
         _run(ctx, X, V[:2], kern, ls, a2, s2, "bf16", flags=gpk.MVM_SUM(2))
+
+
+@pytest.mark.parametrize("kern", [0, 1, 2, 3])
+@pytest.mark.parametrize("shape", [(1, 2, 1), (129, 4, 5), (700, 8, 17), (1000, 11, 24), (4097, 3, 2), (600, 29, 12)])
+def test_symmetric_half_work_mvm_matches_oracle(ctx, kern, shape):
+    """The symmetric half-work MVM (GP_MVM_SYMMETRIC, FP32): each kernel value
+    evaluated once for both row blocks; the FP32 tolerance (1e-5) against the
+    FP64 oracle, including ragged block counts and the diagonal blocks."""
+    from paper_2207_06856_gb300 import gpk
+    N, d, R = shape
+    X, V, _, ls, a2, s2 = workloads.random_problem(N, d, R, seed=N + 11 * d + R, kernel=kern)
+    got = _run(ctx, X, V, kern, ls, a2, s2, "fp32", flags=gpk.MVM_SYMMETRIC)
+    assert _colerr(got, _ref(X, V, kern, ls, a2, s2)) <= TOL["fp32"]
+    got0 = _run(ctx, X, V, kern, ls, a2, s2, "fp32", flags=gpk.MVM_SYMMETRIC, add_noise=False)
+    assert _colerr(got0, _ref(X, V, kern, ls, a2, s2, add_noise=False)) <= TOL["fp32"]
+
+
+def test_symmetric_half_work_mvm_refuses_other_shapes(ctx):
+    from paper_2207_06856_gb300 import gpk
+    X, V, kern, ls, a2, s2 = workloads.random_problem(300, 3, 25, seed=49)
+    with pytest.raises(gpk.GPKError):       # more than 24 right-hand sides
+        _run(ctx, X, V, kern, ls, a2, s2, "fp32", flags=gpk.MVM_SYMMETRIC)
+    Xs = np.random.default_rng(50).standard_normal((300, 3)).astype(np.float32)
+    with pytest.raises(gpk.GPKError):       # not a square operator
+        _run(ctx, Xs, V[:3], kern, ls, a2, s2, "fp32", Xc=X, add_noise=False, flags=gpk.MVM_SYMMETRIC)
+    with pytest.raises(gpk.GPKError):       # FP32 only
+        _run(ctx, X, V[:3], kern, ls, a2, s2, "fp16", flags=gpk.MVM_SYMMETRIC)
+
+
+@pytest.mark.parametrize("sleep", [False, True])
+def test_device_wait_runs_out_and_context_stays_usable(ctx, sleep):
+    """Failure detection without a fault: a bounded mbarrier wait that nothing
+    completes (the wait helpers of the MVM kernels) gives up after its limit,
+    the error word reads GP_ERR_TIMEOUT once, and the context then computes a
+    correct MVM."""
+    import time
+    from paper_2207_06856_gb300 import gpk
+    ctx.check()
+    t0 = time.perf_counter()
+    cyc = ctx.wait_check(5.0, sleep=sleep)
+    assert time.perf_counter() - t0 < 10.0
+    assert cyc >= 2 * 5_000_000          # the limit counts 2 SM cycles per ns
+    with pytest.raises(gpk.GPKError) as e:
+        ctx.check()
+    assert e.value.status == gpk.GP_ERR_TIMEOUT
+    ctx.check()                           # read once, then cleared
+    X, V, kern, ls, a2, s2 = workloads.random_problem(700, 8, 17, seed=3)
+    got = _run(ctx, X, V, kern, ls, a2, s2, "fp16")
+    assert _colerr(got, _ref(X, V, kern, ls, a2, s2)) <= TOL["fp16"]
