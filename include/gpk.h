@@ -304,6 +304,16 @@ typedef struct {
                             definite to the accuracy the solve has reached), the
                             true-residual restart continues the solve with the
                             check_precision MVM.  Needs restarts > 0.                */
+    int refine_precision; /* 0 = off; else the MVM flags (GP_PREC_* | GP_MVM_*) the
+                            solve switches to, for the rest of the solve, at the moment
+                            refine_resid sets                                          */
+    double refine_resid;  /* > 0: switch once the recursive relative residual of every
+                            active column is <= refine_resid (within the run: with an
+                            accurate first MVM and a cheaper refine MVM this relaxes the
+                            operator as the residual falls, whose rounding then moves
+                            the true residual less); 0: switch at the first
+                            true-residual check (the restarts run on the refine MVM:
+                            refinement in the operator; needs restarts > 0)           */
 } gp_cg_opts_t;
 
 /* Host-side statistics (every pointer may be NULL). */

@@ -252,11 +252,19 @@ scalar_kernel(int mode, int stable, const double* __restrict__ part, int nblk, i
         if (__shfl_sync(0xffffffffu, last, 0)) {
             __threadfence();
             int cnt = 0;
-            for (int q = l; q < R; q += 32) cnt += *(volatile const int*)&st[q].active != 0;
+            float rmax = 0.0f;   // largest recursive relative residual of the active columns
+            for (int q = l; q < R; q += 32) {
+                if (*(volatile const int*)&st[q].active != 0) {
+                    ++cnt;
+                    rmax = fmaxf(rmax, (float)*(volatile const double*)&st[q].relres);
+                }
+            }
             cnt = __reduce_add_sync(0xffffffffu, cnt);
+            const unsigned rbits = __reduce_max_sync(0xffffffffu, __float_as_uint(rmax));   // non-negative floats
             if (l == 0) {
                 n_active[0] = cnt;
                 n_active[2] = 0;
+                n_active[3] = (int)rbits;
             }
         }
     }
@@ -430,7 +438,17 @@ int check_cg_args(const gp_hyp_t* hyp, int64_t N, int R, const gp_cg_opts_t* o) 
     GPK_TRY(check_mvm_flags(o->check_precision, false));
     if (o->reorth < GP_REORTH_NONE || o->reorth > GP_REORTH_EUCLID) return GP_ERR_INVALID;
     GPK_TRY(check_mvm_flags(o->precision, false));
+    if (o->refine_precision != 0) {
+        GPK_TRY(check_mvm_flags(o->refine_precision, false));
+        if (!(o->refine_resid >= 0.0) || (o->refine_resid == 0.0 && o->restarts < 1)) return GP_ERR_INVALID;
+    }
     return GP_OK;
+}
+
+// The refine MVM needs its own operator unless it is the solve's or the check's.
+bool refine_own(const gp_cg_opts_t* o) {
+    return o->refine_precision != 0 && o->refine_precision != o->precision &&
+           !(o->restarts > 0 && o->refine_precision == o->check_precision);
 }
 
 }  // namespace
@@ -441,6 +459,7 @@ size_t cg_workspace(const Ctx* ctx, const gp_hyp_t* hyp, int64_t N, int R, int r
     size_t s = c.off + kop_workspace(ctx, hyp, N, N, R, o->precision, true);
     if (o->restarts > 0 && o->check_precision != o->precision)
         s += kop_workspace(ctx, hyp, N, N, R, o->check_precision, true);
+    if (refine_own(o)) s += kop_workspace(ctx, hyp, N, N, R, o->refine_precision, true);
     if (rank > 0) s += woodbury_workspace(ctx, N, rank, R);
     return s;
 }
@@ -458,8 +477,10 @@ int CgSolver::launched(int n) {
 }
 
 int CgSolver::flag_copy() {
-    // [0] active columns, [1] breakdown count of the current run
-    if (cudaMemcpyAsync(flag_host, b.nact, 2 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    // [0] active columns, [1] breakdown count of the current run, [2] 0 (the
+    // scalar step's ticket), [3] largest relative residual of the active columns
+    // (float bits)
+    if (cudaMemcpyAsync(flag_host, b.nact, 4 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return GP_ERR_CUDA;
     if (ev && cudaEventRecord(ev, s) != cudaSuccess) return GP_ERR_CUDA;
     return GP_OK;
@@ -518,7 +539,7 @@ int CgSolver::iterate() {
     const dim3 gdot((unsigned)b.nblk_dot, (unsigned)R);
     const size_t NR = (size_t)N * R;
     // Kd = Ktilde d
-    GPK_TRY(kop_apply(ctx, escalated ? *op_chk : op, b.d, R, b.Kd, N, true, s));
+    GPK_TRY(kop_apply(ctx, escalated ? *op_chk : refined ? *op_ref : op, b.d, R, b.Kd, N, true, s));
     GPK_TRY(dots(b.d, b.Kd, true));   // masked by the flags of the last scalar step
     GPK_TRY(scalar(SC_ALPHA, k));
     update_xr_kernel<<<gcol, 256, 0, s>>>(U, b.r, b.d, b.Kd, N, b.st);
@@ -596,12 +617,22 @@ int CgSolver::setup(Ctx* c, WsCarver& wc, const gp_hyp_t* h, const float* X_, in
         GPK_TRY(kop_prepare(ctx, wc, op_chk_own, &hyp, X, N, X, N, R, o.check_precision, s));
         op_chk = &op_chk_own;
     }
+    op_ref = &op;
+    if (o.refine_precision != 0) {
+        if (refine_own(&o)) {
+            GPK_TRY(kop_prepare(ctx, wc, op_ref_own, &hyp, X, N, X, N, R, o.refine_precision, s));
+            op_ref = &op_ref_own;
+        } else if (o.refine_precision != o.precision) {
+            op_ref = op_chk;
+        }
+    }
     wc_rest = wc;
     vg = vec_grid(ctx, N);
     k = nb0 = restarts = iters = 0;
     last_check = false;
     len_recorded = false;
     escalated = false;
+    refined = false;
     GPK_TRY(dots(B, B, false));
     GPK_TRY(scalar(SC_BNORM, 0));
     return start(o.x0_given != 0, 0);
@@ -611,6 +642,15 @@ int CgSolver::setup(Ctx* c, WsCarver& wc, const gp_hyp_t* h, const float* X_, in
 int CgSolver::step(bool* done) {
     const int n = *flag_host;
     *done = false;
+    if (o.refine_precision != 0 && !refined && o.refine_resid > 0.0 && n > 0) {
+        // relaxation: the rest of the solve on the refine MVM once every active
+        // column's recursive residual is at most refine_resid
+        uint32_t bits;
+        memcpy(&bits, &flag_host[3], sizeof(bits));
+        float rmax;
+        memcpy(&rmax, &bits, sizeof(rmax));
+        if ((double)rmax <= o.refine_resid) refined = true;
+    }
     if (n > 0 && k < o.max_iter) {
         last_check = false;
         return iterate();
@@ -631,6 +671,8 @@ int CgSolver::step(bool* done) {
         // accuracy reached: with escalation the rest of the solve uses the
         // check MVM (the restart below already does).
         if (o.escalate && flag_host[1] > 0 && op_chk != &op) escalated = true;
+        // mixed-precision refinement: the restarts run on the refine MVM
+        if (o.refine_precision != 0 && o.refine_resid == 0.0) refined = true;
         // True-residual check: recompute r = K x - b; columns above tol restart.
         ++restarts;
         nb0 = k;

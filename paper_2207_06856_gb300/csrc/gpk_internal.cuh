@@ -288,13 +288,14 @@ struct CgSolver {
     gp_precond_t pc{};
     int rank = 0, stable = 0, reorth = 0, passes = 1, vg = 1;
     CgBufs b{};
-    KOp op, op_chk_own;
+    KOp op, op_chk_own, op_ref_own;
     KOp* op_chk = nullptr;
+    KOp* op_ref = nullptr;   // iterations after the first true-residual check (refine_precision)
     WsCarver wc_rest{nullptr, 0};
     int* flag_host = nullptr;
     cudaEvent_t ev = nullptr;
     int k = 0, nb0 = 0, restarts = 0, iters = 0;
-    bool last_check = false, len_recorded = false, escalated = false;
+    bool last_check = false, len_recorded = false, escalated = false, refined = false;
 
     int setup(Ctx* c, WsCarver& wc, const gp_hyp_t* h, const float* X, int64_t N, const float* B, int R, float* U,
               const gp_precond_t* pc, const gp_cg_opts_t* o, cudaStream_t s, int* flag_host, cudaEvent_t ev);

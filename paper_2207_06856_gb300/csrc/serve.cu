@@ -449,7 +449,7 @@ int gp_server_create(int device, const gp_server_opts_t* opts, gp_server** out) 
         if (sl->ctx.host_pinned) {
             // pinned scratch: [0] active-column flag, [1] device error word, [16..) column state
             sl->host_flag = sl->ctx.host_pinned;
-            sl->host_err = sl->ctx.host_pinned + 1;
+            sl->host_err = sl->ctx.host_pinned + 8;   // [0, 4): the solver's flag words
             sl->host_state = (gpk::ColState*)(sl->ctx.host_pinned + 16);
         }
         srv->slots.push_back(std::move(sl));

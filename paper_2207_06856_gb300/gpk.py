@@ -79,7 +79,8 @@ class _CgOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("min_iter", ctypes.c_int),
                 ("precision", ctypes.c_int), ("algorithm", ctypes.c_int), ("reorth", ctypes.c_int),
                 ("reorth_passes", ctypes.c_int), ("x0_given", ctypes.c_int), ("restarts", ctypes.c_int),
-                ("check_precision", ctypes.c_int), ("escalate", ctypes.c_int)]
+                ("check_precision", ctypes.c_int), ("escalate", ctypes.c_int), ("refine_precision", ctypes.c_int),
+                ("refine_resid", ctypes.c_double)]
 
 
 class _CgStats(ctypes.Structure):
@@ -369,11 +370,16 @@ def pivchol_precond(ctx: Context, hyp: Hyper, X, rank: int, stream=None) -> Prec
 def cg_solve(ctx: Context, hyp: Hyper, X, B, precond: Precond | None = None, tol: float = 1e-2,
              max_iter: int = 50, min_iter: int = 0, precision="fp16", algorithm: str = "stable",
              reorth: str = "pinv", reorth_passes: int = 1, U=None, flags: int = 0, restarts: int = 4,
-             check_precision="fp32", escalate: bool = True, stream=None):
+             check_precision="fp32", escalate: bool = True, refine_precision=None, refine_resid: float = 0.0,
+             stream=None):
     """gp_cg_solve: (K + sigma^2 I) U = B.  B (R, N) -> (U (R, N), status, info).
     info holds the per-column iterations, relative residuals, alpha/beta
     histories (numpy arrays) and gamma_0.  status is GP_OK,
-    GP_ERR_NOT_CONVERGED or GP_ERR_BREAKDOWN (other errors raise)."""
+    GP_ERR_NOT_CONVERGED or GP_ERR_BREAKDOWN (other errors raise).
+    refine_precision: MVM flags (or a precision name) the solve switches to,
+    once every active column's recursive relative residual is <= refine_resid
+    (> 0), or at the first true-residual check (refine_resid = 0); None keeps
+    the solve's MVM throughout."""
     import torch
     N, d = X.shape
     R = B.shape[0]
@@ -382,7 +388,8 @@ def cg_solve(ctx: Context, hyp: Hyper, X, B, precond: Precond | None = None, tol
                    CG_STABLE if algorithm == "stable" else CG_STANDARD,
                    REORTH[reorth] if isinstance(reorth, str) else int(reorth), int(reorth_passes),
                    1 if U is not None else 0, int(restarts), _check_flags(check_precision, prec),
-                   1 if escalate else 0)
+                   1 if escalate else 0, 0 if refine_precision is None else _check_flags(refine_precision, prec),
+                   float(refine_resid))
     h = hyp.c()
     rank = precond.rank if precond is not None else 0
     need = int(lib().gp_cg_workspace_size(ctypes.byref(h), N, R, rank, ctypes.byref(opts)))

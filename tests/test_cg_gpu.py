@@ -245,3 +245,62 @@ def test_split_fp16_solve_needs_fp32_iteration_count(ctx):
     r = O.kmvm_rows(w.X, rows, U.cpu().numpy().T, _ohyp(w), add_noise=True) - Bt[rows]
     est = np.sqrt(w.N / len(rows) * np.sum(r * r, axis=0)) / np.linalg.norm(Bt, axis=0)
     assert est.max() <= 1.15 * w.tol, est
+
+
+def test_precision_workload_full_size_relaxed_schedule(ctx):
+    """The benchmark's solve with its relaxed MVM schedule: the FP16 MVM with the
+    kernel tile and inputs as hi + lo until every column's recursive residual is
+    <= 0.3 (30 x tol), the single-rounded FP16 MVM after.  The FP64 residual over
+    all 65,536 rows must be <= 1e-2 for every column, and the schedule must need
+    fewer iterations than the single-rounded MVM throughout (the accurate early
+    MVMs keep the true residual close to the recursive one)."""
+    from oracle import cfp64 as C
+    from paper_2207_06856_gb300 import gpk
+    w = workloads.precision()
+    hyp = gpk.Hyper(w.kernel, w.lengthscale, w.outputscale, w.noise)
+    X = _dev(w.X)
+    pc = gpk.pivchol(ctx, hyp, X, w.rank)
+    B = w.rhs()
+    tol = w.tol * (1.0 - STOP_MARGIN)
+    U, st, info = gpk.cg_solve(ctx, hyp, X, _dev(B), pc, tol=tol, max_iter=w.max_iter,
+                               precision=gpk.FP16 | gpk.MVM_PSPLIT | gpk.MVM_XSPLIT, refine_precision="fp16",
+                               refine_resid=30.0 * w.tol)
+    _, st1, info1 = gpk.cg_solve(ctx, hyp, X, _dev(B), pc, tol=tol, max_iter=w.max_iter, precision="fp16")
+    ctx.check()
+    assert st == gpk.GP_OK and st1 == gpk.GP_OK
+    assert info["iters"] < info1["iters"], (info["iters"], info1["iters"])
+    full = C.relative_residual(w.X, U.cpu().numpy().T, B.T, _ohyp(w))
+    assert full.max() <= w.tol, full
+
+
+def test_refine_switch_points(ctx):
+    """refine_resid above every residual switches before the first iteration,
+    so the solve is bit-identical to one on the refine MVM alone; below every
+    residual it never switches (bit-identical to the solve's own MVM); in
+    between the trajectory starts like the first and differs later.  Invalid
+    switch settings are refused."""
+    from paper_2207_06856_gb300 import gpk
+    w = workloads.precision(N=6000)
+    hyp = gpk.Hyper(w.kernel, w.lengthscale, w.outputscale, w.noise)
+    X, B = _dev(w.X), _dev(w.rhs())
+    pc = gpk.pivchol(ctx, hyp, X, w.rank)
+    split = gpk.FP16 | gpk.MVM_PSPLIT | gpk.MVM_XSPLIT
+    kw = dict(tol=w.tol, max_iter=w.max_iter)
+    Ua, _, ia = gpk.cg_solve(ctx, hyp, X, B, pc, precision=split, **kw)
+    Ub, _, ib = gpk.cg_solve(ctx, hyp, X, B, pc, precision="fp16", **kw)
+    Uhi, _, ihi = gpk.cg_solve(ctx, hyp, X, B, pc, precision=split, refine_precision="fp16", refine_resid=1e30, **kw)
+    Ulo, _, ilo = gpk.cg_solve(ctx, hyp, X, B, pc, precision=split, refine_precision="fp16", refine_resid=1e-30,
+                               **kw)
+    Umid, _, imid = gpk.cg_solve(ctx, hyp, X, B, pc, precision=split, refine_precision="fp16", refine_resid=0.3,
+                                 **kw)
+    assert torch.equal(Uhi, Ub) and np.array_equal(ihi["alpha"], ib["alpha"])
+    assert torch.equal(Ulo, Ua) and np.array_equal(ilo["alpha"], ia["alpha"])
+    k = int(np.argmax(np.max(ia["resid_hist"], axis=1) <= 0.3))   # first iterate at or below the switch point
+    assert k > 1
+    assert np.array_equal(imid["alpha"][:k], ia["alpha"][:k])
+    assert not np.array_equal(imid["alpha"], ia["alpha"][:len(imid["alpha"])])
+    with pytest.raises(gpk.GPKError):
+        gpk.cg_solve(ctx, hyp, X, B, pc, precision=split, refine_precision="fp16", refine_resid=-1.0, **kw)
+    with pytest.raises(gpk.GPKError):
+        gpk.cg_solve(ctx, hyp, X, B, pc, precision=split, refine_precision="fp16", refine_resid=0.0, restarts=0,
+                     **kw)
