@@ -444,6 +444,10 @@ typedef struct {
     int max_iter;        /* CG iteration limit (bounds the re-orthogonalisation store) */
     int restarts;        /* FP32 true-residual checks, 0..16                        */
     int reorth;          /* GP_REORTH_*                                             */
+    int refine_precision; /* 0 = off; else the MVM flags CG switches to once every
+                            recursive relative residual is <= refine_resid (> 0), or at
+                            the first true-residual check (0): gp_cg_opts_t's fields */
+    double refine_resid;
 } gp_server_opts_t;
 
 typedef struct {

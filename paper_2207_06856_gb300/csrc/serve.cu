@@ -149,6 +149,8 @@ gp_cg_opts_t cg_opts_of(const gp_server_opts_t& o) {
     c.restarts = o.restarts;
     c.check_precision = GP_PREC_FP32;
     c.escalate = 1;
+    c.refine_precision = o.refine_precision;
+    c.refine_resid = o.refine_resid;
     return c;
 }
 
@@ -159,6 +161,10 @@ int check_opts(const gp_server_opts_t* o) {
     if (o->reorth < GP_REORTH_NONE || o->reorth > GP_REORTH_EUCLID) return GP_ERR_INVALID;
     GPK_TRY(check_mvm_flags(o->precision, false));
     GPK_TRY(check_mvm_flags(o->mean_precision, false));
+    if (o->refine_precision != 0) {
+        GPK_TRY(check_mvm_flags(o->refine_precision, false));
+        if (!(o->refine_resid >= 0.0) || (o->refine_resid == 0.0 && o->restarts < 1)) return GP_ERR_INVALID;
+    }
     return GP_OK;
 }
 

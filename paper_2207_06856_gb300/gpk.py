@@ -101,7 +101,8 @@ class _Hyp(ctypes.Structure):
 class _ServerOpts(ctypes.Structure):
     _fields_ = [("arena_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int), ("rank", ctypes.c_int),
                 ("precision", ctypes.c_int), ("mean_precision", ctypes.c_int), ("tol", ctypes.c_double),
-                ("max_iter", ctypes.c_int), ("restarts", ctypes.c_int), ("reorth", ctypes.c_int)]
+                ("max_iter", ctypes.c_int), ("restarts", ctypes.c_int), ("reorth", ctypes.c_int),
+                ("refine_precision", ctypes.c_int), ("refine_resid", ctypes.c_double)]
 
 
 class _ReqStats(ctypes.Structure):
@@ -583,10 +584,13 @@ def mll_and_grad(ctx: Context, hyp: Hyper, X, y, Z, precond: Precond | None = No
 # ---- S8: serving ------------------------------------------------------------------
 
 
-def _server_opts(arena_bytes, max_slots, rank, precision, mean_precision, tol, max_iter, restarts, reorth):
+def _server_opts(arena_bytes, max_slots, rank, precision, mean_precision, tol, max_iter, restarts, reorth,
+                 refine_precision=None, refine_resid=0.0):
     return _ServerOpts(int(arena_bytes), int(max_slots), int(rank), PRECISIONS.get(precision, precision),
                        PRECISIONS.get(mean_precision, mean_precision), float(tol), int(max_iter), int(restarts),
-                       REORTH.get(reorth, reorth))
+                       REORTH.get(reorth, reorth),
+                       0 if refine_precision is None else PRECISIONS.get(refine_precision, refine_precision),
+                       float(refine_resid))
 
 
 class ServeFuture:
@@ -628,9 +632,10 @@ class Server:
 
     def __init__(self, device: int = 0, arena_bytes: int = 8 << 30, max_slots: int = 8, rank: int = 20,
                  precision=FP16 | MVM_PSPLIT | MVM_XSPLIT, mean_precision="fp32", tol: float = 1e-2,
-                 max_iter: int = 1000, restarts: int = 4, reorth="pinv"):
+                 max_iter: int = 1000, restarts: int = 4, reorth="pinv", refine_precision=None,
+                 refine_resid: float = 0.0):
         self.opts = _server_opts(arena_bytes, max_slots, rank, precision, mean_precision, tol, max_iter, restarts,
-                                 reorth)
+                                 reorth, refine_precision, refine_resid)
         h = _c_void_p()
         _check(lib().gp_server_create(int(device), ctypes.byref(self.opts), ctypes.byref(h)), "gp_server_create")
         self._h = h
