@@ -497,8 +497,10 @@ def run_kmvm(args):
         ms, n = e0.elapsed_time(e1), args.steps
     ctx.check()
     pairs = float(w.N) ** 2
-    ev, tot = gpk.kmvm_tile_count(ctx, hyp, X, precision=args.precision, flags=fl) if args.precision != "fp32" \
-        else ((w.N + 1, 2 * w.N) if args.symmetric else (1, 1))   # symmetric: N (N + 1) / 2 of N^2 pairs
+    if args.skip_tiles:
+        ev, tot = gpk.kmvm_tile_count(ctx, hyp, X, precision=args.precision, flags=fl)
+    else:
+        ev, tot = (w.N + 1, 2 * w.N) if args.symmetric else (1, 1)   # symmetric: N (N + 1) / 2 of N^2 pairs
     print(json.dumps({"mode": "kmvm", "precision": args.precision, "kernel": args.kernel, "rhs": int(B.shape[0]),
                       "inputs": "clustered (16 clusters)" if args.clustered else "precision workload",
                       "skip_tiles": bool(args.skip_tiles), "symmetric": bool(args.symmetric),
