@@ -512,6 +512,81 @@ def run_kmvm(args):
                       "avg_launch_ms": ms / max(n, 1), "pairs_per_s": pairs / (ms / max(n, 1) / 1e3)}), flush=True)
 
 
+def run_minres(args):
+    """Preconditioned MINRES (gp_minres_solve) on the precision workload
+    (N = 65,536, d = 8, RBF, 1 + 16 right-hand sides, rank-100 pivoted
+    Cholesky): time to a relative 2-norm residual of 1e-2 at the FP32
+    true-residual checks (MINRES minimises the P^-1 norm; its recurrence target
+    follows the two norms' ratio after each check), for the single-rounded
+    and the hi + lo FP16 MVM, against CG on the same inputs; both residual norms
+    of every solution recomputed in FP64 over all rows by the oracle (untimed)."""
+    import torch
+    import oracle as O
+    from oracle import cfp64 as C
+    from paper_2207_06856_gb300 import gpk, workloads
+    w = workloads.precision(kernel=gpk.KERNELS[args.kernel])
+    hyp = gpk.Hyper(w.kernel, w.lengthscale, w.outputscale, w.noise)
+    ctx = gpk.Context(0)
+    X = torch.from_numpy(w.X).cuda()
+    Bh = w.rhs()
+    B = torch.from_numpy(Bh).cuda()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    oh = O.Hyp(workloads.KERNEL_NAMES[w.kernel], w.lengthscale, w.outputscale, w.noise)
+    L64, _ = O.pivoted_cholesky(w.X, oh, w.rank)
+    C.build()
+    split = gpk.FP16 | gpk.MVM_PSPLIT | gpk.MVM_XSPLIT
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        ts = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            out = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        return float(np.mean(ts)), out
+
+    def verify(U):
+        Ut = U.cpu().numpy().T.astype(np.float64)
+        res = C.kmvm(w.X, Ut, oh, add_noise=True) - Bh.T.astype(np.float64)
+        Bt = Bh.T.astype(np.float64)
+        rel2 = np.linalg.norm(res, axis=0) / np.linalg.norm(Bt, axis=0)
+        relp = np.sqrt(np.sum(res * O.precond_apply(L64, w.noise, res), axis=0) /
+                       np.sum(Bt * O.precond_apply(L64, w.noise, Bt), axis=0))
+        return float(rel2.max()), float(relp.max())
+
+    out = {}
+    for name, prec in (("minres_fp16_single", "fp16"), ("minres_fp16_hi_lo", split), ("minres_fp32", "fp32")):
+        def solve_m(prec=prec):
+            pc = gpk.pivchol(ctx, hyp, X, w.rank)
+            return gpk.minres_solve(ctx, hyp, X, B, pc, tol=TOL * (1.0 - args.stop_margin), max_iter=MAX_ITER,
+                                    precision=prec, restarts=8, norm="2")
+        t, (U, st, info) = timed(solve_m)
+        r2, rp = verify(U)
+        out[name] = {"s_per_solve": t, "status": int(st), "iters": int(info["iters"]),
+                     "restarts": int(info["restarts"]), "fp64_rel_resid_p_max": rp, "fp64_rel_resid_2_max": r2}
+    for name, prec, ref, rr in (("cg_relaxed", split, "fp16", RELAX_RESID), ("cg_fp16_single", "fp16", None, 0.0)):
+        def solve_c(prec=prec, ref=ref, rr=rr):
+            pc = gpk.pivchol(ctx, hyp, X, w.rank)
+            return gpk.cg_solve(ctx, hyp, X, B, pc, tol=TOL * (1.0 - args.stop_margin), max_iter=MAX_ITER,
+                                precision=prec, refine_precision=ref, refine_resid=rr)
+        t, (U, st, info) = timed(solve_c)
+        r2, rp = verify(U)
+        out[name] = {"s_per_solve": t, "status": int(st), "iters": int(info["iters"]),
+                     "restarts": int(info["restarts"]), "fp64_rel_resid_p_max": rp, "fp64_rel_resid_2_max": r2}
+    print(json.dumps({"mode": "minres", "workload": solve_config(w.N, Bh.shape[0], args.kernel, 1)["workload"],
+                      "tol": TOL * (1.0 - args.stop_margin), "steps": args.steps, "warmup": args.warmup,
+                      "note": "both stop on the 2-norm residual of the FP32 check; MINRES's recurrence on the "
+                              "P^-1 norm (target rescaled at each check)",
+                      "results": out}), flush=True)
+
+
 def run_sumstudy(args):
     """Summation-variant study (Sec. 4.1, Fig. 4b; App. B, Fig. A.1a) on inputs
     shaped like the scale workload (N = 65,536 drawn from its distribution,
@@ -838,7 +913,8 @@ def main():
     ap.add_argument("--extra-diff-steps", type=int, default=4)
     ap.add_argument("--extra-serve-requests", type=int, default=96)
     ap.add_argument("--ref-iters", type=int, default=152)
-    ap.add_argument("--mode", default="solve", choices=["solve", "kmvm", "serve", "diff", "scale", "vjp", "sumstudy"])
+    ap.add_argument("--mode", default="solve",
+                    choices=["solve", "kmvm", "serve", "diff", "scale", "vjp", "sumstudy", "minres"])
     ap.add_argument("--diff-steps", type=int, default=20)
     ap.add_argument("--diff-n", type=int, default=262144)
     ap.add_argument("--diff-tol", type=float, default=1.0)
@@ -876,6 +952,8 @@ def main():
         run_vjp(args)
     elif args.mode == "sumstudy":
         run_sumstudy(args)
+    elif args.mode == "minres":
+        run_minres(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -350,6 +350,61 @@ GPK_API int gp_cg_solve(gp_ctx* ctx, const gp_hyp_t* hyp, const float* X, int64_
                         float* U, const gp_precond_t* precond, const gp_cg_opts_t* opts, gp_cg_stats_t* stats,
                         void* stream);
 
+/* ---- NEXT #4: low-precision preconditioned MINRES (Conclusion, future work) --
+ * MINRES (Paige and Saunders' Lanczos-based minimum-residual method) for
+ * (K + sigma^2 I) U = B with the same kernel MVM engines and the same
+ * pivoted-Cholesky preconditioner P as gp_cg_solve: the Conclusion names the
+ * low-precision and mixed-precision approach of the paper as applicable to
+ * MINRES.  Over the Krylov space of P^-1 Ktilde it minimises the residual in
+ * the P^-1 norm, ||r||_{P^-1} = sqrt(r^T P^-1 r) (the 2-norm without a
+ * preconditioner); each column runs its own Lanczos process and QR
+ * factorisation (Givens rotations) in FP64 on the device, all columns share
+ * one MVM per iteration.  A column stops when ||r_k||_{P^-1} / ||b||_{P^-1}
+ * <= tol (the recurrence's estimate).  With restarts > 0, when every column
+ * has stopped, r = b - Ktilde x is recomputed with the check_precision MVM and
+ * the columns whose true P^-1-norm residual is above tol restart from their
+ * current x (fresh Lanczos process).                                          */
+typedef struct {
+    double tol;          /* relative residual in the P^-1 norm                      */
+    int max_iter;        /* 1 .. 1000 (iterations over all runs)                    */
+    int precision;       /* MVM flags: GP_PREC_* | GP_MVM_* option bits              */
+    int restarts;        /* true-residual checks, 0 .. 16                           */
+    int check_precision; /* MVM flags of the checks and of the final residual       */
+    int norm;            /* GP_MINRES_NORM_P (0): tol applies to ||r||_{P^-1}; or
+                            GP_MINRES_NORM_2 (1): tol applies to ||r||_2 / ||b||_2 at
+                            the true-residual checks (and for the status); after a
+                            check each column's recurrence stops at
+                            tol * 0.95 * (P^-1-norm / 2-norm of its recomputed
+                            residual), the norms' observed ratio.  Needs restarts > 0. */
+} gp_minres_opts_t;
+#define GP_MINRES_NORM_P 0
+#define GP_MINRES_NORM_2 1
+
+typedef struct {
+    int iters;           /* iterations run (over all runs)                          */
+    int converged;       /* columns whose final residual (in the opts' norm) is <= tol */
+    int breakdowns;      /* columns stopped because r^T P^-1 r was negative or NaN  */
+    int restarts;        /* true-residual restarts performed                        */
+    int* col_iters;      /* [R] or null: iterations of each column                  */
+    double* rel_resid;   /* [R] or null: final ||Ktilde x - b||_2 / ||b||_2 (check MVM) */
+    double* rel_resid_p; /* [R] or null: final ||Ktilde x - b||_{P^-1} / ||b||_{P^-1}   */
+    double* resid_hist;  /* [(max_iter + 1) * R] or null: the recurrence's P^-1-norm
+                            relative residual after each iteration (k * R + c)      */
+} gp_minres_stats_t;
+
+/* B, U: R x N row-major (right-hand side c at c * N), device, FP32; U is
+ * overwritten with the solution (x_0 = 0).  precond may be null (P = I).
+ * Workspace from the context (gp_minres_workspace_size).  Returns GP_OK when
+ * every column meets tol, GP_ERR_NOT_CONVERGED when some did not within
+ * max_iter (U and stats still valid), GP_ERR_BREAKDOWN when a column's
+ * r^T P^-1 r was not positive (that column keeps its last iterate),
+ * GP_ERR_INVALID / GP_ERR_WORKSPACE / GP_ERR_CUDA / GP_ERR_TIMEOUT otherwise. */
+GPK_API size_t gp_minres_workspace_size(const gp_hyp_t* hyp, int64_t N, int R, int rank,
+                                        const gp_minres_opts_t* opts);
+GPK_API int gp_minres_solve(gp_ctx* ctx, const gp_hyp_t* hyp, const float* X, int64_t N, const float* B, int R,
+                            float* U, const gp_precond_t* precond, const gp_minres_opts_t* opts,
+                            gp_minres_stats_t* stats, void* stream);
+
 /* ---- S7: backward of the kernel MVM (gradient of a bilinear form) ----------
  * grad_theta[0..d+2) = d/d(l_1..l_d, a^2, sigma^2) of  q = sum_c u_c^T Ktilde w_c,
  * and, when grad_X is not NULL, grad_X = dq/dX (device, N x d row-major).

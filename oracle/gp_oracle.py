@@ -47,7 +47,7 @@ __all__ = [
     "mll_grad_exact", "quad_form_grad", "pseudo_loss_grad",
     "lse_dot", "LSEBreakdown",
     "pivoted_cholesky", "woodbury_core", "precond_apply", "precond_logdet",
-    "cg_standard", "cg_stable", "cg_mbcg", "CGResult",
+    "cg_standard", "cg_stable", "cg_mbcg", "CGResult", "minres", "MinresResult",
     "lanczos_tridiagonal", "slq_quadrature",
     "max_distance", "relative_residual",
 ]
@@ -569,6 +569,96 @@ def cg_mbcg(matmat, B, precond=None, tol=1e-6, max_iter=None) -> list:
         active = active & (rel > tol)
     for c in range(R):
         res[c].x = X[:, c]
+    return res
+
+
+# ---------------------------------------------------------------------------
+# MINRES (Conclusion: a further iterative method for the low-precision approach)
+# ---------------------------------------------------------------------------
+
+@dataclass
+class MinresResult:
+    x: np.ndarray
+    iters: int
+    resid_p: list = field(default_factory=list)   # ||r_k||_{P^-1} / ||b||_{P^-1} from the recurrence
+    alphas: list = field(default_factory=list)    # Lanczos diagonal
+    betas: list = field(default_factory=list)     # Lanczos off-diagonal beta_{k+1}
+    breakdown: bool = False
+
+
+def minres(matvec, b, precond=None, tol=1e-6, max_iter=None) -> MinresResult:
+    """Preconditioned MINRES (Paige and Saunders' method), one right-hand
+    side, x_0 = 0.  The paper only names MINRES as a target of its approach
+    (Conclusion); this is the textbook method, written out.
+
+    With P SPD and M = P^-1 (`precond` applies P^-1), the Lanczos process of
+    M A in the P inner product gives unnormalised vectors r_k (r_1 = b) with
+    y_k = M r_k, beta_k = sqrt(r_k^T y_k), v_k = y_k / beta_k (P-orthonormal),
+        r_{k+1} = A v_k - alpha_k r_k / beta_k - (beta_k / beta_{k-1}) r_{k-1},
+        alpha_k = v_k^T A v_k,
+    i.e. the tridiagonal T_k (alpha on the diagonal, beta off it).  x_k
+    minimises ||b - A x||_M over the Krylov space: with the QR factorisation
+    of the (k+1) x k tridiagonal by Givens rotations, the new rotation
+    (c_k, s_k) annihilates beta_{k+1}; the directions w_k = (v_k - eps_k w_{k-2}
+    - delta_k w_{k-1}) / gamma_k and x_k = x_{k-1} + tau_k w_k with tau_k = c_k
+    phibar_{k-1}, and ||r_k||_M = |phibar_k| = |s_k phibar_{k-1}|.
+    """
+    b = np.asarray(b, dtype=np.float64)
+    P = precond or _identity
+    N = b.shape[0]
+    max_iter = N if max_iter is None else max_iter
+    x = np.zeros(N)
+    r_prev = np.zeros(N)           # r_{k-1}
+    r_cur = b.copy()               # r_k
+    y = P(r_cur)
+    beta1 = math.sqrt(float(r_cur @ y))
+    res = MinresResult(x=x, iters=0)
+    res.resid_p.append(1.0 if beta1 > 0 else 0.0)
+    if beta1 == 0.0:
+        return res
+    beta_prev, beta = 0.0, beta1
+    # rotation state: the previous rotation (c, s), the entries it leaves in
+    # the next column (dbar: the rotated sub-diagonal, eps: the fill-in two rows up)
+    c, s = -1.0, 0.0
+    dbar, eps = 0.0, 0.0
+    phibar = beta1
+    w_prev2 = np.zeros(N)          # w_{k-2}
+    w_prev = np.zeros(N)           # w_{k-1}
+    k = 0
+    while res.resid_p[-1] > tol and k < max_iter:
+        v = y / beta
+        Av = matvec(v)
+        u = Av - (beta / beta_prev) * r_prev if beta_prev > 0.0 else Av
+        alpha = float(v @ u)
+        u = u - (alpha / beta) * r_cur
+        r_prev, r_cur = r_cur, u
+        y = P(r_cur)
+        ry = float(r_cur @ y)
+        if not (ry >= 0.0) or not math.isfinite(ry):
+            res.breakdown = True
+            break
+        beta_prev, beta = beta, math.sqrt(ry)
+        # apply the previous rotation to the new column (alpha, beta) of T
+        eps_k = eps                          # fill-in from two rotations ago
+        delta = c * dbar + s * alpha         # entry above the diagonal
+        gbar = s * dbar - c * alpha          # diagonal before the new rotation
+        eps = s * beta                       # fill-in for the next column
+        dbar = -c * beta                     # sub-diagonal carried to the next column
+        gamma = math.hypot(gbar, beta)
+        gamma = max(gamma, 1e-300)
+        c, s = gbar / gamma, beta / gamma    # the rotation annihilating beta_{k+1}
+        tau = c * phibar
+        phibar = s * phibar
+        w = (v - eps_k * w_prev2 - delta * w_prev) / gamma
+        x = x + tau * w
+        w_prev2, w_prev = w_prev, w
+        k += 1
+        res.alphas.append(alpha)
+        res.betas.append(beta)
+        res.resid_p.append(abs(phibar) / beta1)
+        if beta == 0.0:
+            break
+    res.x, res.iters = x, k
     return res
 
 

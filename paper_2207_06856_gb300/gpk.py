@@ -92,6 +92,18 @@ class _CgStats(ctypes.Structure):
                 ("lanczos_len", ctypes.POINTER(ctypes.c_int))]
 
 
+class _MinresOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
+                ("restarts", ctypes.c_int), ("check_precision", ctypes.c_int), ("norm", ctypes.c_int)]
+
+
+class _MinresStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("breakdowns", ctypes.c_int),
+                ("restarts", ctypes.c_int), ("col_iters", ctypes.POINTER(ctypes.c_int)),
+                ("rel_resid", ctypes.POINTER(ctypes.c_double)), ("rel_resid_p", ctypes.POINTER(ctypes.c_double)),
+                ("resid_hist", ctypes.POINTER(ctypes.c_double))]
+
+
 class _Hyp(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("d", ctypes.c_int),
                 ("lengthscale", ctypes.POINTER(ctypes.c_float)),
@@ -156,6 +168,11 @@ def _declare(lib):
         "gp_pivchol_precond": (_c_int, [_c_void_p, ctypes.POINTER(_Hyp), _c_void_p, _c_i64, _c_int, _c_void_p,
                                         _c_void_p, _c_void_p, ctypes.POINTER(_c_int), _c_void_p]),
         "gp_cg_workspace_size": (_c_size, [ctypes.POINTER(_Hyp), _c_i64, _c_int, _c_int, ctypes.POINTER(_CgOpts)]),
+        "gp_minres_workspace_size": (_c_size, [ctypes.POINTER(_Hyp), _c_i64, _c_int, _c_int,
+                                               ctypes.POINTER(_MinresOpts)]),
+        "gp_minres_solve": (_c_int, [_c_void_p, ctypes.POINTER(_Hyp), _c_void_p, _c_i64, _c_void_p, _c_int, _c_void_p,
+                                     ctypes.POINTER(_Precond), ctypes.POINTER(_MinresOpts),
+                                     ctypes.POINTER(_MinresStats), _c_void_p]),
         "gp_cg_solve": (_c_int, [_c_void_p, ctypes.POINTER(_Hyp), _c_void_p, _c_i64, _c_void_p, _c_int, _c_void_p,
                                  ctypes.POINTER(_Precond), ctypes.POINTER(_CgOpts), ctypes.POINTER(_CgStats),
                                  _c_void_p]),
@@ -424,6 +441,50 @@ def cg_solve(ctx: Context, hyp: Hyper, X, B, precond: Precond | None = None, tol
             "col_iters": col_iters, "rel_resid": rel, "gamma0": g0,
             "alpha": al.reshape(max_iter, R)[:it], "beta": be.reshape(max_iter, R)[:it],
             "resid_hist": rh.reshape(max_iter + 1, R)[:it + 1], "lanczos_len": lz}
+    return U, st, info
+
+
+def minres_solve(ctx: Context, hyp: Hyper, X, B, precond: Precond | None = None, tol: float = 1e-2,
+                 max_iter: int = 200, precision="fp16", flags: int = 0, restarts: int = 4, check_precision="fp32",
+                 norm: str = "p", stream=None):
+    """gp_minres_solve: (K + sigma^2 I) U = B by preconditioned MINRES.
+    B (R, N) -> (U (R, N), status, info).  tol applies to the residual in the
+    P^-1 norm (norm="p") or, at the true-residual checks, in the 2-norm
+    (norm="2"); info holds per-column iterations, the final 2-norm and P^-1-norm
+    relative residuals (recomputed with the check MVM) and the recurrence's
+    P^-1-norm residual history.  status is GP_OK, GP_ERR_NOT_CONVERGED or
+    GP_ERR_BREAKDOWN (other errors raise)."""
+    import torch
+    N, d = X.shape
+    R = B.shape[0]
+    prec = (PRECISIONS[precision] if isinstance(precision, str) else int(precision)) | int(flags)
+    opts = _MinresOpts(float(tol), int(max_iter), prec, int(restarts), _check_flags(check_precision, prec),
+                       {"p": 0, "2": 1}[norm])
+    h = hyp.c()
+    rank = precond.rank if precond is not None else 0
+    need = int(lib().gp_minres_workspace_size(ctypes.byref(h), N, R, rank, ctypes.byref(opts)))
+    if need == 0:
+        raise GPKError(GP_ERR_INVALID, "gp_minres_workspace_size")
+    if need > ctx.workspace_bytes:
+        ctx.reserve(need)
+    U = torch.empty((R, N), dtype=torch.float32, device=B.device)
+    col_iters = np.zeros(R, np.int32)
+    rel = np.zeros(R, np.float64)
+    relp = np.zeros(R, np.float64)
+    rh = np.zeros((max_iter + 1) * R, np.float64)
+    P = ctypes.POINTER
+    stats = _MinresStats(0, 0, 0, 0, col_iters.ctypes.data_as(P(ctypes.c_int)), rel.ctypes.data_as(P(ctypes.c_double)),
+                         relp.ctypes.data_as(P(ctypes.c_double)), rh.ctypes.data_as(P(ctypes.c_double)))
+    pc = precond.c() if precond is not None else _Precond(None, None, 0)
+    st = lib().gp_minres_solve(ctx.ptr, ctypes.byref(h), _dev_ptr(X, "X", (N, d)), N, _dev_ptr(B, "B", (R, N)), R,
+                               _dev_ptr(U, "U", (R, N)), ctypes.byref(pc), ctypes.byref(opts), ctypes.byref(stats),
+                               _stream_ptr(stream))
+    if st not in (GP_OK, GP_ERR_NOT_CONVERGED, GP_ERR_BREAKDOWN):
+        _check(st, "gp_minres_solve")
+    it = int(stats.iters)
+    info = {"iters": it, "converged": int(stats.converged), "breakdowns": int(stats.breakdowns),
+            "restarts": int(stats.restarts), "col_iters": col_iters, "rel_resid": rel, "rel_resid_p": relp,
+            "resid_hist": rh.reshape(max_iter + 1, R)[:it + 1]}
     return U, st, info
 
 

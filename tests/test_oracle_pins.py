@@ -444,3 +444,86 @@ def test_mbcg_equals_alg1_column_by_column():
         np.testing.assert_allclose(res[c].betas[:12], ref.betas[:12], rtol=1e-9)
         assert abs(res[c].gamma0 - ref.gamma0) <= 1e-12 * abs(ref.gamma0)
         assert np.linalg.norm(res[c].x - exact[:, c]) <= 1e-6 * np.linalg.norm(exact[:, c])
+
+
+# ---- MINRES (Conclusion: a further iterative method for the approach) -------------------
+
+def _spd_problem(N=60, seed=0):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((N, N))
+    A = A @ A.T / N + 0.05 * np.eye(N)
+    return A, rng.standard_normal(N)
+
+
+@pytest.mark.parametrize("precond", [False, True])
+def test_minres_iterates_match_the_library_routine(precond):
+    """k steps of the oracle's MINRES equal k steps of scipy's MINRES (the
+    library routine of the same method), with and without an SPD
+    preconditioner (here P = diag(A): P^-1 applied as r / d)."""
+    sla = pytest.importorskip("scipy.sparse.linalg")
+    import inspect
+    A, b = _spd_problem()
+    d = np.diag(A).copy()
+    kw = "rtol" if "rtol" in inspect.signature(sla.minres).parameters else "tol"
+    M = sla.LinearOperator(A.shape, matvec=lambda r: r / d) if precond else None
+    for k in (1, 4, 12, 30):
+        res = O.minres(lambda v: A @ v, b, precond=(lambda r: r / d) if precond else None, tol=0.0, max_iter=k)
+        xs, _ = sla.minres(A, b, M=M, maxiter=k, **{kw: 0.0})
+        assert res.iters == k
+        # rounding-order differences grow with k on this condition number (~100); a
+        # wrong coefficient or sign shows at the 1e-2 level from the first steps
+        assert np.linalg.norm(res.x - xs) <= (1e-12 if k < 10 else 1e-7) * np.linalg.norm(xs), k
+
+
+@pytest.mark.parametrize("precond", [False, True])
+def test_minres_minimises_the_preconditioned_residual_over_the_krylov_space(precond):
+    """The defining property: x_k = argmin ||b - A x||_M over the Krylov space
+    span{M b, (M A) M b, ..., (M A)^{k-1} M b}, M = P^-1 -- brute force by least
+    squares on an orthonormal basis of that space, in the M inner product (M =
+    G G^T, ||r||_M = ||G^T r||).  Also: the recurrence's phibar / beta_1 is that
+    minimum relative to ||b||_M at every k."""
+    A, b = _spd_problem(N=40, seed=3)
+    Mm = np.diag(1.0 / np.diag(A)) if precond else np.eye(40)
+    G = np.linalg.cholesky(Mm)
+    for k in (1, 3, 6, 10):
+        res = O.minres(lambda v: A @ v, b, precond=lambda r: Mm @ r, tol=0.0, max_iter=k)
+        Kb = [Mm @ b]
+        for _ in range(k - 1):
+            Kb.append(Mm @ (A @ Kb[-1]))
+        Q, _ = np.linalg.qr(np.array(Kb).T)
+        c, *_ = np.linalg.lstsq(G.T @ A @ Q, G.T @ b, rcond=None)
+        x_star = Q @ c
+        assert np.linalg.norm(res.x - x_star) <= 1e-8 * np.linalg.norm(x_star), k
+        r = b - A @ res.x
+        rel = math.sqrt(r @ (Mm @ r)) / math.sqrt(b @ (Mm @ b))
+        assert abs(res.resid_p[-1] - rel) <= 1e-10, (k, res.resid_p[-1], rel)
+
+
+def test_minres_finite_termination_and_monotone_residual():
+    """In exact arithmetic MINRES solves an N x N SPD system in at most N
+    steps; its P^-1-norm residual never increases (it minimises over growing
+    spaces).  Small N, FP64: the exact solution to 1e-10."""
+    A, b = _spd_problem(N=25, seed=5)
+    res = O.minres(lambda v: A @ v, b, tol=1e-13, max_iter=200)
+    x = np.linalg.solve(A, b)
+    assert np.linalg.norm(res.x - x) <= 1e-9 * np.linalg.norm(x)
+    assert all(r1 <= r0 * (1 + 1e-12) for r0, r1 in zip(res.resid_p, res.resid_p[1:]))
+
+
+def test_minres_on_the_gp_operator_with_the_woodbury_preconditioner():
+    """The configuration the GPU path runs: Ktilde of a GP kernel, P the rank-k
+    pivoted-Cholesky preconditioner applied by Eq. woodbury; the solution
+    converges to the Cholesky solve and the recurrence's norm matches the
+    recomputed P^-1-norm residual."""
+    rng = np.random.default_rng(7)
+    X = rng.standard_normal((300, 3))
+    hyp = O.Hyp("rbf", np.array([0.9, 1.1, 1.0]), 1.2, 0.05)
+    Kt = O.ktilde_dense(X, hyp)
+    L, _ = O.pivoted_cholesky(X, hyp, 20)
+    b = rng.standard_normal(300)
+    P = lambda r: O.precond_apply(L, hyp.noise, r)
+    res = O.minres(lambda v: Kt @ v, b, precond=P, tol=1e-10, max_iter=300)
+    x = O.cholesky_solve(X, hyp, b[:, None])[:, 0]
+    assert np.linalg.norm(res.x - x) <= 1e-7 * np.linalg.norm(x)
+    r = b - Kt @ res.x
+    assert abs(math.sqrt(r @ P(r)) / math.sqrt(b @ P(b)) - res.resid_p[-1]) <= 1e-9
