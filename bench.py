@@ -327,10 +327,23 @@ def run_ours(args):
         variants[vname] = {"avg_launch_ms": v_ms / max(v_n, 1), "achieved": v_ach, "frac": v_ach / peak_meas,
                            "traffic": KMVM_TRAFFIC_BYTES.get((args.kernel, args.precision, N, R, vflags))}
     mixed = head[3] is not None
+    traffic = KMVM_TRAFFIC_BYTES.get((args.kernel, args.precision, N, R, 0))
+    launch_mix = None
+    if mixed:
+        # launches of each configuration in a timed solve: the hi + lo MVM up to the first
+        # iterate whose largest recursive residual is <= RELAX_RESID, the single-rounded one after
+        rh = np.max(infos[-1]["resid_hist"], axis=1)
+        n_it = int(infos[-1]["iters"])
+        below = np.nonzero(rh[:n_it + 1] <= RELAX_RESID)[0]
+        k_sw = int(below[0]) if below.size else n_it
+        launch_mix = {"hi_lo": k_sw, "single": n_it - k_sw}
+        t_hl = KMVM_TRAFFIC_BYTES.get((args.kernel, args.precision, N, R, gpk.MVM_PSPLIT | gpk.MVM_XSPLIT))
+        traffic = None if (traffic is None or t_hl is None or n_it == 0) else \
+            (k_sw * t_hl + (n_it - k_sw) * traffic) / n_it
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_meas, "unit": "Gpairs/s",
                 "frac": achieved / peak_meas,
-                # the timed region mixes two launch configurations; each one's DRAM bytes are under variants
-                "traffic": None if mixed else KMVM_TRAFFIC_BYTES.get((args.kernel, args.precision, N, R, 0)),
+                # mixed schedule: the launch-weighted mean of the two configurations' ncu bytes
+                "traffic": traffic, "launch_mix": launch_mix,
                 "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                 "kernel": "kmvm_tp_kernel (tcgen05 S = X_i X_j^T and transposed value product "
                           "O^T = Vt_j P^T over row-tile pairs; kernel function on the SFU)"
@@ -360,6 +373,27 @@ def run_ours(args):
             arms[name] = {"s_per_solve": float(np.mean(ts)), "iters": int(inf[-1]["iters"]),
                           "restarts": int(inf[-1]["restarts"]),
                           "first_run_iters": int(np.max(inf[-1]["lanczos_len"]))}
+        # preconditioned MINRES on the single-rounded FP16 MVM, to the same 2-norm target
+        if not args.arms or "minres_fp16_single" in args.arms.split(","):
+            def solve_mr():
+                pc = gpk.pivchol(ctx, hyp, X, w.rank)
+                return gpk.minres_solve(ctx, hyp, X, B, pc, tol=TOL * (1.0 - args.stop_margin), max_iter=MAX_ITER,
+                                        precision=args.precision, restarts=8, norm="2")
+            solve_mr()
+            ts_mr = []
+            for _ in range(max(1, min(args.steps, 2))):
+                flush.fill_(1.0)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                _, st_mr, inf_mr = solve_mr()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts_mr.append(e0.elapsed_time(e1) / 1e3)
+            arms["minres_fp16_single"] = {"s_per_solve": float(np.mean(ts_mr)), "iters": int(inf_mr["iters"]),
+                                          "restarts": int(inf_mr["restarts"]), "status": int(st_mr),
+                                          "rel_resid_max": float(np.max(inf_mr["rel_resid"]))}
 
     # --- end to end through the public API with host buffers ----------------------------
     e2e_times = []
