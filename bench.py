@@ -507,7 +507,8 @@ def run_kmvm(args):
     out = torch.empty_like(B)
     fl = (gpk.MVM_ONE_TILE if args.one_tile else 0) | (gpk.MVM_PSPLIT if args.psplit else 0) | \
         (gpk.MVM_HALF_EXP if args.half_exp else 0) | (gpk.MVM_SKIP_TILES if args.skip_tiles else 0) | \
-        (gpk.MVM_SYMMETRIC if args.symmetric else 0) | (gpk.MVM_XSPLIT if args.xsplit else 0)
+        (gpk.MVM_SYMMETRIC if args.symmetric else 0) | (gpk.MVM_XSPLIT if args.xsplit else 0) | \
+        (gpk.MVM_FP32_PV if args.fp32_pv else 0)
     if args.clustered:
         # compact-support case: 16 clusters of 4,096 points (d = 8, within-cluster std 0.3 lengthscales,
         # centres 20 lengthscales apart), stored cluster by cluster
@@ -541,7 +542,7 @@ def run_kmvm(args):
                       "evaluated_fraction": ev / tot,
                       "evaluated_pairs_per_s": pairs * ev / tot / (ms / max(n, 1) / 1e3),
                       "engine": "one-tile" if args.one_tile else "pair", "psplit": bool(args.psplit),
-                      "half_exp": bool(args.half_exp), "xsplit": bool(args.xsplit),
+                      "half_exp": bool(args.half_exp), "xsplit": bool(args.xsplit), "fp32_pv": bool(args.fp32_pv),
                       "launches": n,
                       "avg_launch_ms": ms / max(n, 1), "pairs_per_s": pairs / (ms / max(n, 1) / 1e3)}), flush=True)
 
@@ -733,8 +734,9 @@ def serve_measure(args, n_requests, n_calib=None):
     pin = gpk.Server.pinned
     inputs = [(gpk.Hyper(r.kernel, r.lengthscale, r.outputscale, r.noise), pin(r.X), pin(r.y), pin(r.Xstar))
               for r in reqs]
+    sprec = gpk.FP16 | gpk.MVM_XSPLIT | (gpk.MVM_FP32_PV if args.serve_schedule == "fp32pv" else gpk.MVM_PSPLIT)
     srv = gpk.Server(0, arena_bytes=int(args.serve_arena_gb * (1 << 30)), max_slots=args.serve_slots, rank=20,
-                     precision=gpk.FP16 | gpk.MVM_PSPLIT | gpk.MVM_XSPLIT, mean_precision="fp32", tol=TOL,
+                     precision=sprec, mean_precision="fp32", tol=TOL,
                      max_iter=1000, restarts=4,
                      refine_precision="fp16" if args.serve_schedule == "relaxed" else None,
                      refine_resid=RELAX_RESID if args.serve_schedule == "relaxed" else 0.0)
@@ -787,9 +789,11 @@ def serve_measure(args, n_requests, n_calib=None):
                                f"trace), Poisson arrivals at "
                                f"{args.serve_load:.2f}x saturated rate, N log-uniform [1k, 200k], d in {{4,8,16}}, "
                                "RBF/Matern-3/2, 1024 test points, FP16 tensor-core MVM ("
-                               + ("kernel tile and inputs as hi + lo until every residual is <= 30 x tol, "
-                                  "single-rounded after" if args.serve_schedule == "relaxed" else
-                                  "kernel tile and inputs as hi + lo") + ") + stable CG to 1e-2, rank 20",
+                               + {"relaxed": "kernel tile and inputs as hi + lo until every residual is <= 30 x tol, "
+                                             "single-rounded after",
+                                  "split": "kernel tile and inputs as hi + lo",
+                                  "fp32pv": "inputs as hi + lo, FP32 kernel values and value product"}[
+                                   args.serve_schedule] + ") + stable CG to 1e-2, rank 20",
                    "slots": args.serve_slots, "arena_gb": args.serve_arena_gb},
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
         "mean_ms": float(lat.mean()), "solves_per_s": len(reqs) / wall, "saturated_solves_per_s": sat,
@@ -963,9 +967,11 @@ def main():
     ap.add_argument("--clustered", action="store_true", help="kmvm mode: clustered inputs (16 far-apart clusters)")
     ap.add_argument("--symmetric", action="store_true", help="kmvm mode: FP32 symmetric half-work MVM")
     ap.add_argument("--xsplit", action="store_true", help="kmvm mode: inputs carried as hi + lo")
-    ap.add_argument("--serve-schedule", default="split", choices=["relaxed", "split"],
-                    help="serving CG MVM: hi + lo throughout (default), or hi + lo until the residual is "
-                         "30 x tol then single-rounded (fails to converge on low-noise requests of the trace)")
+    ap.add_argument("--fp32-pv", action="store_true", help="kmvm mode: FP32 value product (1 to 4 right-hand sides)")
+    ap.add_argument("--serve-schedule", default="fp32pv", choices=["relaxed", "split", "fp32pv"],
+                    help="serving CG MVM: FP32 kernel values and value product with hi + lo inputs (fp32pv, the "
+                         "default), hi + lo tile and inputs throughout (split), or hi + lo until the residual is "
+                         "30 x tol then single-rounded (relaxed; fails on low-noise requests)")
     ap.add_argument("--arms", default="", help="comma-separated subset of the comparison arms (default: all)")
     ap.add_argument("--nrhs", type=int, default=0, help="kmvm mode: use the first NRHS right-hand sides (0: all 17)")
     ap.add_argument("--serve-requests", type=int, default=512)

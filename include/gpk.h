@@ -116,6 +116,15 @@ extern "C" {
                                        shapes: GP_ERR_UNSUPPORTED (non-square,
                                        R > 24, d > 32) or GP_ERR_INVALID (with a
                                        non-FP32 precision). */
+#define GP_MVM_FP32_PV    0x400000  /* FP16, pair engine, R <= 4: S on the tensor
+                                       cores as usual, the kernel values kept in
+                                       FP32 and the value product sum_j k_ij v_j
+                                       done by the epilogue threads in FP32 FMAs
+                                       (v as hi + lo), instead of rounding P to
+                                       FP16 for a tensor-core product whose
+                                       M = 128 rows would hold 1..4 right-hand
+                                       sides.  For the single-column solves of
+                                       serving.  Other shapes: GP_ERR_UNSUPPORTED. */
 #define GP_MVM_ONE_TILE     0x4000  /* tensor-core MVM on the one-row-tile engine
                                        (P V with M = 128 rows, N = R) instead of
                                        the default pair engine (transposed

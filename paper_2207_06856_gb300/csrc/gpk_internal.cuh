@@ -89,6 +89,7 @@ struct OperandLayout {
     int vsplit = 0;  // 1: right-hand sides carried as hi + lo (extra P.V product)
     int psplit = 0;  // 1: kernel tile carried as hi + lo (extra P.V product; BF16)
     int half_exp = 0;  // 1: S rounded to FP16 by the MMA, 2^s in FP16 (RBF, FP16, k_pad 16)
+    int fp32_pv = 0;   // 1: value product in FP32 on the epilogue threads (FP16, pair engine, R <= 4)
 };
 OperandLayout make_layout(int d, int prec, int xsplit, int vsplit, int psplit);
 float kernel_input_scale(int kernel);   // c such that x_hat = c x / l
@@ -110,6 +111,8 @@ int launch_bbox(Ctx* ctx, const float* X, int64_t N, int d, unsigned* bb, cudaSt
 int launch_prep_x_f32(Ctx* ctx, const float* X, int64_t N, int64_t N_pad, int d, int dp, const ScaleVec& inv,
                       float* Xs, cudaStream_t s);
 int launch_v_colmax(Ctx* ctx, const float* V, int64_t N, int R, unsigned* cmax_bits, cudaStream_t s);
+int launch_v_pack32(Ctx* ctx, const float* V, int64_t N, int64_t N_pad, int R, const unsigned* cmax_bits,
+                    double outputscale, float* V32, float* outscale, cudaStream_t s);
 // Vt rows: [0, R_pad) the (hi) cast, [R_pad, 2 R_pad) the lo parts when vsplit.
 int launch_v_cast(Ctx* ctx, int prec, int scale_mode, int vsplit, const float* V, int64_t N, int64_t N_pad, int R,
                   int R_pad, const unsigned* cmax_bits, double outputscale, void* Vt, float* outscale,

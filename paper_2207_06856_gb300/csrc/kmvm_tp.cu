@@ -35,7 +35,8 @@
 // special-function work), 16 TMA producer, 17 S issuer and TMEM owner, 18
 // value-product issuer (one issuing warp serialises too many high-latency
 // tcgen05 and mbarrier operations per tile pair; see tp_mma_s).  TMEM: S of
-// tile 0 [0,128), S of tile 1 [128,256), O^T [256,512).  The epilogue signals
+// tile 0 [0,128), S of tile 1 [128,256), O^T [256,512) (with the FP32 value
+// product, which has no O^T, a second S buffer there).  The epilogue signals
 // each barrier once per warp (after __syncwarp), never once per thread.
 // With HS (GP_MVM_HALF_EXP) the S product accumulates in FP16 and the
 // epilogue evaluates 2^s in FP16 pairs.  Shared memory: the X_j / Vt_j stage ring first, then the two
@@ -71,12 +72,15 @@ constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kTmemO = 256;
 constexpr uint32_t kPKBlock = (uint32_t)kPairRows * 128u;   // one 64-column K-block of P: 256 rows x 128 B
 constexpr int kMaxSmemBytes = 227 * 1024;   // opt-in maximum per CTA (512 B kept for static shared memory)
+constexpr uint32_t kSpvVBytes = 128u * 4u * 4u;   // FP32 value product: 128 columns x 4 rows of FP32 v
 
 struct TpParams {
     int n_ip, n_jt, n_split, n_items;
     int k_pad, rv;        // rv: rows of Vt per tile (R_pad, or 2 R_pad with the hi + lo split)
     int stages, xi_bufs;
     int psplit;           // 1: P carried as hi + lo
+    int nrhs;             // right-hand sides in use (the FP32 value product: <= 4)
+    int spv;              // 1: FP32 value product; the V map is FP32, 128 columns x 4 rows per box
     int diag;             // square Matern-1/2 operator: P_ii = 0 on chip (exact diagonal added later)
     int64_t ld_part;      // n_ip * 256
     float* partial;       // [n_split][rv][ld_part]
@@ -89,8 +93,8 @@ struct TpParams {
 struct TpBarriers {
     uint64_t full[kMaxStages];
     uint64_t empty[kMaxStages];
-    uint64_t s_full[2];     // per row tile (epilogue warpgroup)
-    uint64_t s_empty[2];
+    uint64_t s_full[4];     // [S buffer * 2 + row tile]; a second S buffer only with the FP32 value product
+    uint64_t s_empty[4];
     uint64_t p_full[2];     // per P buffer: tile slot (single P) or K-block (hi + lo P)
     uint64_t p_empty[2];
     uint64_t o_full;
@@ -145,10 +149,14 @@ __device__ void tp_producer(const TpParams& p, const CUtensorMap* tmA, const CUt
             const uint32_t st = fills % S, u = fills / S;
             if (u > 0 && !ptx::mbar_wait(&bars.empty[st], (u - 1) & 1, p.limit_ns)) { ok = false; break; }
             uint8_t* sx = sSt + st * (xbytes + vtbytes);
-            ptx::mbar_arrive_expect_tx(&bars.full[st], xbytes + vtbytes);
+            ptx::mbar_arrive_expect_tx(&bars.full[st], xbytes + (p.spv ? kSpvVBytes : vtbytes));
             ptx::tma_load_2d(sx, tmB, &bars.full[st], 0, jt * kBN);
-            ptx::tma_load_2d(sx + xbytes, tmV, &bars.full[st], jt * kBN, 0);
-            ptx::tma_load_2d(sx + xbytes + kblk, tmV, &bars.full[st], jt * kBN + 64, 0);
+            if (p.spv) {
+                ptx::tma_load_2d(sx + xbytes, tmV, &bars.full[st], jt * kBN, 0);
+            } else {
+                ptx::tma_load_2d(sx + xbytes, tmV, &bars.full[st], jt * kBN, 0);
+                ptx::tma_load_2d(sx + xbytes + kblk, tmV, &bars.full[st], jt * kBN + 64, 0);
+            }
             ++fills;
         }
         if (!ok) break;
@@ -201,19 +209,21 @@ __device__ void tp_mma_s(const TpParams& p, TpBarriers& bars, const uint8_t* sSt
         const uint32_t aXi = ptx::smem_u32(sXi) + (uint32_t)xb * 2u * xbytes;
         for (int jt = j0; jt < j1; ++jt) {
             if (!tile_on(p, ip, jt)) continue;
-            if (g > 0 && !(warp_wait(&bars.s_empty[0], (g - 1) & 1, p.limit_ns) &&
-                           warp_wait(&bars.s_empty[1], (g - 1) & 1, p.limit_ns))) { ok = false; break; }
+            // S buffer of this tile (two with the FP32 value product, whose O^T columns are free)
+            const uint32_t nb = p.spv ? 2u : 1u, buf = g % nb, use = g / nb;
+            if (use > 0 && !(warp_wait(&bars.s_empty[2 * buf], (use - 1) & 1, p.limit_ns) &&
+                             warp_wait(&bars.s_empty[2 * buf + 1], (use - 1) & 1, p.limit_ns))) { ok = false; break; }
             if (!warp_wait(&bars.full[st], ph, p.limit_ns)) { ok = false; break; }
             ptx::tc_fence_after();
             const uint32_t aXj = aSt + st * stage_bytes;
             for (int w = 0; w < 2; ++w) {
                 for (int kk = 0; kk < ksteps; ++kk) {
                     const uint32_t koff = (uint32_t)kk * 32u;
-                    ptx::mma_f16_ss_elect(tmem + (uint32_t)w * 128u,
+                    ptx::mma_f16_ss_elect(tmem + buf * 256u + (uint32_t)w * 128u,
                                           ptx::smem_desc_at(hi_x, aXi + (uint32_t)w * xbytes + koff),
                                           ptx::smem_desc_at(hi_x, aXj + koff), id_s, kk > 0 ? 1u : 0u);
                 }
-                ptx::mma_commit_elect(&bars.s_full[w]);
+                ptx::mma_commit_elect(&bars.s_full[2 * buf + w]);
             }
             if (++st == S) { st = 0; ph ^= 1u; }
             ++g;
@@ -454,6 +464,108 @@ __device__ void tp_epilogue(const TpParams& p, TpBarriers& bars, const uint8_t* 
     if (!ok) record_error(p.err, DEV_TIMEOUT);
 }
 
+// The FP32 value product (GP_MVM_FP32_PV, 1 to 4 right-hand sides): the
+// epilogue keeps its kernel values in FP32 and forms sum_j k_ij v_j itself
+// with FP32 FMAs, v_j read in FP32 from the stage (TMA box of 128 columns x 4
+// rows; this warpgroup's 64 columns; broadcast 16-byte reads).  No P in shared
+// memory and no value-product MMAs: a tensor-core product with 1 to 4 useful
+// rows of its M = 128 would cost as much as one with 64.  Each warp releases
+// the stage after its reads (16 arrivals), and writes its row sums of the item
+// to the partial rows ch * R_pad + r, which the split reduction adds up.
+template <int KIND, int RN>
+__device__ void tp_epilogue_spv(const TpParams& p, TpBarriers& bars, const uint8_t* sSt, uint32_t xbytes,
+                                uint32_t vtbytes, uint32_t tmem, int wg, int wq, int lane) {
+    const int tl = wg & 1, ch = wg >> 1;
+    const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
+    const int row = wq * 32 + lane;
+    const uint32_t S = (uint32_t)p.stages;
+    const uint32_t stage_bytes = xbytes + vtbytes;
+    const int Rp = p.rv >> 1;
+    constexpr int R = RN;   // columns 1, 2 or 4 (3 runs as 4: the fourth row of v is zero)
+    uint32_t gt = 0, st = 0, ph = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < p.n_items; item += gridDim.x) {
+        int ip, sp, j0, j1;
+        item_range(p, item, ip, sp, j0, j1);
+        const int it = 2 * ip + tl;
+        float acc[RN];
+#pragma unroll
+        for (int r = 0; r < RN; ++r) acc[r] = 0.0f;
+        uint32_t t = 0;
+        for (int jt = j0; jt < j1; ++jt) {
+            if (!tile_on(p, ip, jt)) continue;
+            const uint32_t g = gt + t, buf = g & 1u;
+            // hinted waits: a spinning warp would take the issue slots of the warps computing
+            // beside it and of the S issuer on its scheduler (this epilogue is issue-bound)
+            if (!__all_sync(0xffffffffu,
+                            ptx::mbar_wait_sleep(&bars.s_full[2 * buf + tl], (g >> 1) & 1, p.limit_ns) &&
+                                ptx::mbar_wait_sleep(&bars.full[st], ph, p.limit_ns))) {
+                ok = false;
+                break;
+            }
+            ptx::tc_fence_after();
+            const uint32_t tS = tmem + lane_off + buf * 256u + (uint32_t)tl * 128u + (uint32_t)ch * 64u;
+            const bool dtile = (KIND == GP_KERNEL_MATERN12) && p.diag && (jt == it);
+            const float* vb = reinterpret_cast<const float*>(sSt + st * stage_bytes + xbytes) + ch * 64;
+            // one 32-column half of S at a time (the register budget of 608 threads); the
+            // buffer is released after the second load, while S of the next tile is
+            // already being formed in the other one
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                uint32_t rr[32];
+                ptx::tmem_ld32(tS + 32u * (uint32_t)hh, rr);
+                ptx::tmem_wait_ld();
+                ptx::tmem_reg_fence(rr);
+                if (hh == 1) {
+                    ptx::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) ptx::mbar_arrive(&bars.s_empty[2 * buf + tl]);
+                }
+#pragma unroll
+                for (int c4 = 0; c4 < 4; ++c4) {      // 16-byte chunk c: columns [8 c, 8 c + 8) of the 64
+                    const int c = 4 * hh + c4;
+                    float kv[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int q = 8 * c + e;
+                        float k = kernel_from_s<KIND>(__uint_as_float(rr[8 * c4 + e]));
+                        if constexpr (KIND == GP_KERNEL_MATERN12) {
+                            if (dtile && ch * 64 + q == row) k = 0.0f;
+                        }
+                        kv[e] = k;
+                    }
+#pragma unroll
+                    for (int r = 0; r < RN; ++r) {
+                        {
+                            const float4 va = *reinterpret_cast<const float4*>(vb + r * 128 + 8 * c);
+                            const float4 vc = *reinterpret_cast<const float4*>(vb + r * 128 + 8 * c + 4);
+                            acc[r] = fmaf(kv[0], va.x, acc[r]);
+                            acc[r] = fmaf(kv[1], va.y, acc[r]);
+                            acc[r] = fmaf(kv[2], va.z, acc[r]);
+                            acc[r] = fmaf(kv[3], va.w, acc[r]);
+                            acc[r] = fmaf(kv[4], vc.x, acc[r]);
+                            acc[r] = fmaf(kv[5], vc.y, acc[r]);
+                            acc[r] = fmaf(kv[6], vc.z, acc[r]);
+                            acc[r] = fmaf(kv[7], vc.w, acc[r]);
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&bars.empty[st]);   // this warp is done with the stage's Vt
+            if (++st == S) { st = 0; ph ^= 1u; }
+            ++t;
+        }
+        if (!ok) break;
+#pragma unroll
+        for (int r = 0; r < RN; ++r)
+            p.partial[((int64_t)sp * p.rv + ch * Rp + r) * p.ld_part + (int64_t)ip * kPairRows + tl * kBM + row] =
+                acc[r];
+        gt += t;
+    }
+    if (!ok) record_error(p.err, DEV_TIMEOUT);
+}
+
 struct TpSmem {
     uint32_t xbytes, vtbytes, stage_bytes, pbuf;
     int stages, xi_bufs;
@@ -480,7 +592,7 @@ __host__ __device__ inline TpSmem tp_smem(int k_pad, int rv, int psplit) {
     return m;
 }
 
-template <int KIND, int BF16, int PSPLIT, int HS>
+template <int KIND, int BF16, int PSPLIT, int HS, int SPV>
 __global__ void __launch_bounds__(kThreads, 1)
 kmvm_tp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ CUtensorMap tmV, const TpParams p) {
@@ -498,11 +610,13 @@ kmvm_tp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kMaxStages; ++s) {
             ptx::mbar_init(&bars.full[s], 1);
-            ptx::mbar_init(&bars.empty[s], 1);
+            ptx::mbar_init(&bars.empty[s], SPV ? kEpiWarps : 1);   // FP32 product: each epilogue warp
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < 4; ++b) {
             ptx::mbar_init(&bars.s_full[b], 1);
             ptx::mbar_init(&bars.s_empty[b], 8);                // the 8 warps of a row tile (one arrival each)
+        }
+        for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(&bars.xi_full[b], 1);
             ptx::mbar_init(&bars.xi_empty[b], 1);
             ptx::mbar_init(&bars.p_full[b], PSPLIT ? 8 : 16);   // K-block: 2 warpgroups; tile: all 4 (per warp)
@@ -532,9 +646,13 @@ kmvm_tp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         tp_mma_s(p, bars, sSt, sXi, m.xbytes, m.vtbytes, tmem,
                  HS ? ptx::idesc_f16_dh(kBM, kBN) : ptx::idesc_f16(kBM, kBN, BF16));
     } else if (warp == kPvWarp) {
-        tp_mma_pv<PSPLIT>(p, bars, sSt, sP, m.xbytes, m.vtbytes, tmem, ptx::idesc_f16(kBM, kPairRows, BF16));
+        if constexpr (!SPV)
+            tp_mma_pv<PSPLIT>(p, bars, sSt, sP, m.xbytes, m.vtbytes, tmem, ptx::idesc_f16(kBM, kPairRows, BF16));
     } else {
-        tp_epilogue<KIND, BF16, PSPLIT, HS>(p, bars, sP, tmem, warp >> 2, warp & 3, lane);
+        if constexpr (SPV > 0)
+            tp_epilogue_spv<KIND, SPV>(p, bars, sSt, m.xbytes, m.vtbytes, tmem, warp >> 2, warp & 3, lane);
+        else
+            tp_epilogue<KIND, BF16, PSPLIT, HS>(p, bars, sP, tmem, warp >> 2, warp & 3, lane);
     }
     ptx::tc_fence_before();
     __syncthreads();
@@ -542,11 +660,11 @@ kmvm_tp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     if (warp == kMmaWarp) ptx::tmem_dealloc(tmem, kTmemCols);
 }
 
-template <int KIND, int BF16, int PSPLIT, int HS = 0>
+template <int KIND, int BF16, int PSPLIT, int HS = 0, int SPV = 0>
 cudaError_t launch_tp_typed(const TcPlan& plan, const TpParams& prm, const CUtensorMap& a, const CUtensorMap& b,
                             const CUtensorMap& v, cudaStream_t s) {
     const TpSmem m = tp_smem(prm.k_pad, prm.rv, PSPLIT);
-    auto kfn = kmvm_tp_kernel<KIND, BF16, PSPLIT, HS>;
+    auto kfn = kmvm_tp_kernel<KIND, BF16, PSPLIT, HS, SPV>;
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m.total);
     if (e != cudaSuccess) return e;
     kfn<<<plan.grid, kThreads, m.total, s>>>(a, b, v, prm);
@@ -605,6 +723,8 @@ int launch_kmvm_tp(Ctx* ctx, const TcPlan& plan, const OperandLayout& L, const M
     prm.k_pad = plan.k_pad;
     prm.rv = plan.rv;
     prm.psplit = L.psplit;
+    prm.nrhs = a.R;
+    prm.spv = L.fp32_pv ? 1 : 0;
     const TpSmem m = tp_smem(plan.k_pad, plan.rv, L.psplit);
     prm.stages = m.stages;
     prm.xi_bufs = m.xi_bufs;
@@ -630,8 +750,26 @@ int launch_kmvm_tp(Ctx* ctx, const TcPlan& plan, const OperandLayout& L, const M
             e = L.psplit ? launch_tp_typed<K, 0, 1>(plan, prm, tmA, tmB, tmV, s)                     \
                          : launch_tp_typed<K, 0, 0>(plan, prm, tmA, tmB, tmV, s);                    \
         break;
+    const bool spv = L.fp32_pv != 0;
+    if (spv && (bf || L.psplit || hs || a.R > 4 || plan.rv != 2 * plan.R_pad)) return GP_ERR_UNSUPPORTED;
     if (hs) {
         e = launch_tp_typed<GP_KERNEL_RBF, 0, 0, 1>(plan, prm, tmA, tmB, tmV, s);
+    } else if (spv) {
+        // accumulators for 1, 2 or 4 columns (3 runs as 4 on a zero fourth row of v)
+#define GPK_TP_SPV(K)                                                                            \
+    case K:                                                                                      \
+        e = a.R == 1 ? launch_tp_typed<K, 0, 0, 0, 1>(plan, prm, tmA, tmB, tmV, s)               \
+          : a.R == 2 ? launch_tp_typed<K, 0, 0, 0, 2>(plan, prm, tmA, tmB, tmV, s)               \
+                     : launch_tp_typed<K, 0, 0, 0, 4>(plan, prm, tmA, tmB, tmV, s);              \
+        break;
+        switch (a.kernel) {
+            GPK_TP_SPV(GP_KERNEL_RBF)
+            GPK_TP_SPV(GP_KERNEL_MATERN32)
+            GPK_TP_SPV(GP_KERNEL_MATERN12)
+            GPK_TP_SPV(GP_KERNEL_MATERN52)
+            default: return GP_ERR_INVALID;
+        }
+#undef GPK_TP_SPV
     } else switch (a.kernel) {
         GPK_TP_CASE(GP_KERNEL_RBF)
         GPK_TP_CASE(GP_KERNEL_MATERN32)

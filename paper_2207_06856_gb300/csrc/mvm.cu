@@ -85,8 +85,9 @@ int check_mvm_flags(int flags, bool allow_noise) {
     if (prec != GP_PREC_FP32 && prec != GP_PREC_FP16 && prec != GP_PREC_BF16) return GP_ERR_INVALID;
     const int known = 0xff | GP_MVM_ADD_NOISE | GP_MVM_XSPLIT | GP_MVM_NO_XSPLIT | GP_MVM_SCALE_SQRT_N |
                       GP_MVM_VSPLIT | GP_MVM_BF16_SINGLE | GP_MVM_ONE_TILE | GP_MVM_PSPLIT | GP_MVM_HALF_EXP |
-                      GP_MVM_SKIP_TILES | GP_MVM_SUM_MASK | GP_MVM_SYMMETRIC;
+                      GP_MVM_SKIP_TILES | GP_MVM_SUM_MASK | GP_MVM_SYMMETRIC | GP_MVM_FP32_PV;
     if ((flags & GP_MVM_SYMMETRIC) && prec != GP_PREC_FP32) return GP_ERR_INVALID;
+    if ((flags & GP_MVM_FP32_PV) && prec != GP_PREC_FP16) return GP_ERR_INVALID;
     const int sum = (flags & GP_MVM_SUM_MASK) >> 18;
     if (sum > 4 || (sum && prec != GP_PREC_FP16)) return GP_ERR_INVALID;
     if (flags & ~known) return GP_ERR_INVALID;
@@ -108,7 +109,7 @@ static int kop_plan(const Ctx* ctx, KOp& op, const gp_hyp_t* hyp, int64_t Nr, in
     op.sum = (flags & GP_MVM_SUM_MASK) >> 18;
     if (op.sum) {
         // summation-variant study: the CUDA-core FP16 engine on the SIMT engine's scaled inputs
-        if (R > 8 || (flags & (GP_MVM_SKIP_TILES | GP_MVM_HALF_EXP | GP_MVM_PSPLIT | GP_MVM_ONE_TILE)))
+        if (R > 8 || (flags & (GP_MVM_SKIP_TILES | GP_MVM_HALF_EXP | GP_MVM_PSPLIT | GP_MVM_ONE_TILE | GP_MVM_FP32_PV)))
             return GP_ERR_UNSUPPORTED;
         op.sp = simt_plan(ctx, Nr, Nc, hyp->d, R);
         if (op.sp.dp > 32) return GP_ERR_UNSUPPORTED;
@@ -158,6 +159,10 @@ static int kop_plan(const Ctx* ctx, KOp& op, const gp_hyp_t* hyp, int64_t Nr, in
         if (flags & GP_MVM_HALF_EXP) {
             if (bf || !pair || psplit || op.lay.k_pad != 16 || hyp->kernel != GP_KERNEL_RBF) return GP_ERR_UNSUPPORTED;
             op.lay.half_exp = 1;
+        }
+        if (flags & GP_MVM_FP32_PV) {
+            if (bf || !pair || psplit || op.lay.half_exp || R > 4) return GP_ERR_UNSUPPORTED;
+            op.lay.fp32_pv = 1;
         }
         op.tp = pair ? tp_plan(ctx, Nr, Nc, Rc, op.lay.k_pad, vsplit) : tc_plan(ctx, Nr, Nc, Rc, op.lay.k_pad);
     } else {
@@ -272,6 +277,17 @@ int kop_apply(Ctx* ctx, KOp& op, const float* V, int R, float* out, int64_t ld_o
             pl.R_pad = ((rc + 15) / 16) * 16;
             if (pl.engine == 1) pl.rv = pl.R_pad * (op.lay.vsplit ? 2 : 1);
             GPK_TRY(launch_v_colmax(ctx, Vc, op.Nc, rc, op.cmax, s));
+            if (pl.engine == 1 && op.lay.fp32_pv) {
+                // FP32 value product: v in FP32 (4 rows, in the FP16 Vt buffer's space, which
+                // holds 2 x 16 FP16 rows), one TMA box of 128 columns x 4 rows per stage
+                GPK_TRY(launch_v_pack32(ctx, Vc, op.Nc, pl.Nc_pad, rc, op.cmax, op.a2, (float*)op.Vt, op.outscale,
+                                        s));
+                GPK_TRY(encode_tmap_2d(&op.tmV, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, op.Vt, pl.Nc_pad, 4, pl.Nc_pad * 4,
+                                       128, 4, CU_TENSOR_MAP_SWIZZLE_NONE));
+                GPK_TRY(launch_kmvm_tp(ctx, pl, op.lay, a, op.tmA, op.tmB, op.tmV, op.outscale, op.partial,
+                                       op.skip ? op.mask : nullptr, s));
+                continue;
+            }
             GPK_TRY(launch_v_cast(ctx, op.prec, (op.flags & GP_MVM_SCALE_SQRT_N) ? 1 : 0, op.lay.vsplit, Vc, op.Nc,
                                   pl.Nc_pad, rc, pl.R_pad, op.cmax, op.a2, op.Vt, op.outscale, s));
             const CUtensorMapDataType dt =

@@ -259,6 +259,35 @@ __global__ void v_cast_kernel(const float* __restrict__ V, int64_t N, int64_t N_
     }
 }
 
+// FP32 right-hand sides for the FP32 value product of the pair engine:
+// V32 (4 rows x N_pad, row stride N_pad) = V (R x N) zero-padded in rows and
+// columns; outscale = a^2 (the epilogue's sums are of unscaled v), or 0 with
+// DEV_NONFINITE recorded for a column holding a non-finite value.
+__global__ void v_pack32_kernel(const float* __restrict__ V, int64_t N, int64_t N_pad, int R,
+                                const unsigned* __restrict__ cmax_bits, float a2, float* __restrict__ V32,
+                                float* __restrict__ outscale, int* err) {
+    const int c = blockIdx.y;
+    bool ok = true;
+    if (c < R) ok = __uint_as_float(cmax_bits[c]) <= 3.0e38f;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        outscale[c] = (c < R && ok) ? a2 : 0.0f;
+        if (!ok) atomicCAS(err, 0, (int)DEV_NONFINITE);
+    }
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N_pad; j += (int64_t)gridDim.x * blockDim.x)
+        V32[(int64_t)c * N_pad + j] = (c < R && ok && j < N) ? V[(int64_t)c * N + j] : 0.0f;
+}
+
+int launch_v_pack32(Ctx* ctx, const float* V, int64_t N, int64_t N_pad, int R, const unsigned* cmax_bits,
+                    double outputscale, float* V32, float* outscale, cudaStream_t s) {
+    if (R > 4) return GP_ERR_UNSUPPORTED;
+    const int64_t want = (N_pad + 255) / 256;
+    const unsigned blocks = (unsigned)(want < 1024 ? want : 1024);
+    v_pack32_kernel<<<dim3(blocks, 4), 256, 0, s>>>(V, N, N_pad, R, cmax_bits, (float)outputscale, V32, outscale,
+                                                     ctx->dev_err);
+    ctx->launches++;
+    return cudaGetLastError() == cudaSuccess ? GP_OK : GP_ERR_CUDA;
+}
+
 int launch_v_cast(Ctx* ctx, int prec, int scale_mode, int vsplit, const float* V, int64_t N, int64_t N_pad, int R,
                   int R_pad, const unsigned* cmax_bits, double outputscale, void* Vt, float* outscale,
                   cudaStream_t s) {

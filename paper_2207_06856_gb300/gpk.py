@@ -49,6 +49,7 @@ MVM_PSPLIT = 0x8000
 MVM_HALF_EXP = 0x10000
 MVM_SKIP_TILES = 0x20000
 MVM_SYMMETRIC = 0x200000
+MVM_FP32_PV = 0x400000
 
 
 def MVM_SUM(scheme: int) -> int:
@@ -686,13 +687,15 @@ class Server:
     Each request solves (K + sigma^2 I) v = y with the stable preconditioned CG
     and returns mu* = K(X*, X) v.  Inputs are copied into page-locked host
     tensors at submit so the library's uploads are asynchronous.  The default
-    CG precision is FP16 tensor-core operands with the kernel tile and the
-    inputs carried as hi + lo: over the serving workload's range of noise
-    levels it needs the FP32 iteration count, where a single FP16 rounding of
-    the kernel tile can leave the operator too inexact for CG to converge."""
+    CG MVM forms S on the tensor cores from FP16 inputs carried as hi + lo and
+    keeps the kernel values and the one-column value product in FP32
+    (MVM_FP32_PV): over the serving workload's range of noise levels a single
+    FP16 rounding of the kernel tile can leave the operator too inexact for CG
+    to converge, and for one right-hand side the FP32 product is also twice as
+    fast as the hi + lo FP16 tile on the tensor cores."""
 
     def __init__(self, device: int = 0, arena_bytes: int = 8 << 30, max_slots: int = 8, rank: int = 20,
-                 precision=FP16 | MVM_PSPLIT | MVM_XSPLIT, mean_precision="fp32", tol: float = 1e-2,
+                 precision=FP16 | MVM_XSPLIT | MVM_FP32_PV, mean_precision="fp32", tol: float = 1e-2,
                  max_iter: int = 1000, restarts: int = 4, reorth="pinv", refine_precision=None,
                  refine_resid: float = 0.0):
         self.opts = _server_opts(arena_bytes, max_slots, rank, precision, mean_precision, tol, max_iter, restarts,

@@ -465,3 +465,36 @@ def test_device_wait_runs_out_and_context_stays_usable(ctx, sleep):
     X, V, kern, ls, a2, s2 = workloads.random_problem(700, 8, 17, seed=3)
     got = _run(ctx, X, V, kern, ls, a2, s2, "fp16")
     assert _colerr(got, _ref(X, V, kern, ls, a2, s2)) <= TOL["fp16"]
+
+
+@pytest.mark.parametrize("kern", [0, 1, 2, 3])
+@pytest.mark.parametrize("shape", [(1, 2, 1), (300, 3, 1), (1000, 8, 2), (4097, 4, 4), (2500, 16, 3)])
+@pytest.mark.parametrize("xsplit", [False, True])
+def test_fp32_value_product_matches_oracle(ctx, kern, shape, xsplit):
+    """GP_MVM_FP32_PV (1 to 4 right-hand sides): the kernel values stay FP32 and
+    the products are FP32 FMAs, so only the FP16 rounding of the inputs remains
+    (the FP16 tolerance); with the inputs as hi + lo the MVM is FP32-accurate
+    up to the two-term norm representation (1e-4)."""
+    from paper_2207_06856_gb300 import gpk
+    N, d, R = shape
+    X, V, _, ls, a2, s2 = workloads.random_problem(N, d, R, seed=N + 7 * d + R, kernel=kern)
+    fl = gpk.MVM_FP32_PV | (gpk.MVM_XSPLIT if xsplit else 0)   # without: the engine's default input split
+    got = _run(ctx, X, V, kern, ls, a2, s2, "fp16", flags=fl)
+    err = _colerr(got, _ref(X, V, kern, ls, a2, s2))
+    assert err <= (1e-4 if xsplit else TOL["fp16"]), err
+    if N > 1:   # rectangular operator (the predictive-mean shape), rows at new points: coincident
+        # points would put Matern-1/2's kink at r = 0 under the distance's rounding
+        Xr = np.random.default_rng(N).standard_normal((N // 2 + 1, d)).astype(np.float32)
+        got = _run(ctx, Xr, V, kern, ls, a2, s2, "fp16", Xc=X, add_noise=False, flags=fl)
+        assert _colerr(got, _ref(Xr, V, kern, ls, a2, s2, Xc=X, add_noise=False)) <= (1e-4 if xsplit else TOL["fp16"])
+
+
+def test_fp32_value_product_refusals(ctx):
+    from paper_2207_06856_gb300 import gpk
+    X, V, kern, ls, a2, s2 = workloads.random_problem(500, 4, 5, seed=3)
+    with pytest.raises(gpk.GPKError):       # more than 4 right-hand sides
+        _run(ctx, X, V, kern, ls, a2, s2, "fp16", flags=gpk.MVM_FP32_PV)
+    with pytest.raises(gpk.GPKError):       # FP16 only
+        _run(ctx, X, V[:2], kern, ls, a2, s2, "bf16", flags=gpk.MVM_FP32_PV)
+    with pytest.raises(gpk.GPKError):       # not with the hi + lo kernel tile
+        _run(ctx, X, V[:2], kern, ls, a2, s2, "fp16", flags=gpk.MVM_FP32_PV | gpk.MVM_PSPLIT)

@@ -71,9 +71,10 @@ def test_serve_fp32_matches_exact_posterior_mean(gpk):
 @pytest.mark.gpu
 @pytest.mark.parametrize("relaxed", [False, True])
 def test_serve_fp16_within_cg_bound(gpk, relaxed):
-    """The served configurations (FP16 tensor-core MVM with hi + lo tile and
-    inputs, or that MVM until every residual is <= 0.3 and the single-rounded
-    one after; CG to 1e-2, rank 20):
+    """The served configurations (S from hi + lo FP16 inputs on the tensor
+    cores with the FP32 value product -- the default -- or that MVM until every
+    residual is <= 0.3 and the single-rounded FP16 one after; CG to 1e-2,
+    rank 20):
     the reported residual is <= 1e-2 and the mean is within the bound that
     residual implies: mu - mu_exact = K* Ktilde^{-1} r, so
     ||mu - mu_exact|| <= ||K* Ktilde^{-1}||_2 ||r||, ||r|| = rel_resid ||y||
