@@ -320,7 +320,10 @@ typedef struct {
                             active column is <= refine_resid (within the run: with an
                             accurate first MVM and a cheaper refine MVM this relaxes the
                             operator as the residual falls, whose rounding then moves
-                            the true residual less); 0: switch at the first
+                            the true residual less; after a switch below the starting
+                            residual a guard returns to the solve's MVM for good if the
+                            largest residual has not halved within max(20, k_switch / 4)
+                            iterations of the switch or has doubled); 0: switch at the first
                             true-residual check (the restarts run on the refine MVM:
                             refinement in the operator; needs restarts > 0)           */
 } gp_cg_opts_t;

@@ -633,6 +633,9 @@ int CgSolver::setup(Ctx* c, WsCarver& wc, const gp_hyp_t* h, const float* X_, in
     len_recorded = false;
     escalated = false;
     refined = false;
+    relax_off = false;
+    k_sw = 0;
+    r_sw = 0.0f;
     GPK_TRY(dots(B, B, false));
     GPK_TRY(scalar(SC_BNORM, 0));
     return start(o.x0_given != 0, 0);
@@ -642,14 +645,31 @@ int CgSolver::setup(Ctx* c, WsCarver& wc, const gp_hyp_t* h, const float* X_, in
 int CgSolver::step(bool* done) {
     const int n = *flag_host;
     *done = false;
-    if (o.refine_precision != 0 && !refined && o.refine_resid > 0.0 && n > 0) {
-        // relaxation: the rest of the solve on the refine MVM once every active
-        // column's recursive residual is at most refine_resid
+    if (o.refine_precision != 0 && o.refine_resid > 0.0 && n > 0 && !relax_off) {
         uint32_t bits;
         memcpy(&bits, &flag_host[3], sizeof(bits));
         float rmax;
         memcpy(&rmax, &bits, sizeof(rmax));
-        if ((double)rmax <= o.refine_resid) refined = true;
+        if (!refined) {
+            // relaxation: the refine MVM once every active column's recursive
+            // residual is at most refine_resid
+            if ((double)rmax <= o.refine_resid) {
+                refined = true;
+                k_sw = k;
+                r_sw = rmax;
+            }
+        } else {
+            // stagnation guard, for a switch made after the residual fell below its start
+            // (early CG residuals rise well above it): on the cheaper operator the largest
+            // residual must halve within max(20, k_sw / 4) iterations and never double;
+            // otherwise (its rounding is too large for this system) the rest of the solve
+            // returns to the solve's MVM
+            const int W = k_sw / 4 > 20 ? k_sw / 4 : 20;
+            if (r_sw < 1.0f && (rmax > 2.0f * r_sw || (k - k_sw >= W && rmax > 0.5f * r_sw))) {
+                refined = false;
+                relax_off = true;
+            }
+        }
     }
     if (n > 0 && k < o.max_iter) {
         last_check = false;

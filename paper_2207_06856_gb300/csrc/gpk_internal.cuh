@@ -299,6 +299,9 @@ struct CgSolver {
     cudaEvent_t ev = nullptr;
     int k = 0, nb0 = 0, restarts = 0, iters = 0;
     bool last_check = false, len_recorded = false, escalated = false, refined = false;
+    bool relax_off = false;   // the relaxed MVM stalled and was given up for this solve
+    int k_sw = 0;             // iteration of the switch to the refine MVM
+    float r_sw = 0.0f;        // largest active residual at the switch
 
     int setup(Ctx* c, WsCarver& wc, const gp_hyp_t* h, const float* X, int64_t N, const float* B, int R, float* U,
               const gp_precond_t* pc, const gp_cg_opts_t* o, cudaStream_t s, int* flag_host, cudaEvent_t ev);
