@@ -346,7 +346,28 @@ gram_kernel(const float* __restrict__ ZB, int nb, int R, const float* __restrict
         rv[q] = i < N ? r[(int64_t)c * N + i] : 0.0f;
     }
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    for (int j = 0; j < nb; ++j) {
+    // four basis vectors per step: their 32 loads per thread in flight together
+    // (the sums of each vector in the same order as one at a time)
+    int j = 0;
+    for (; j + 4 <= nb; j += 4) {
+        const float* z0 = ZB + ((int64_t)j * R + c) * N;
+        const int64_t stride = (int64_t)R * N;
+        float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int q = 0; q < kDotPerThread; ++q) {
+            const int64_t i = base + q * kDotThreads + threadIdx.x;
+            if (i < N) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) a[u] = fmaf(z0[u * stride + i], rv[q], a[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            for (int o = 16; o > 0; o >>= 1) a[u] += __shfl_xor_sync(0xffffffffu, a[u], o);
+            if (l == 0) sred[w * nb + j + u] = a[u];
+        }
+    }
+    for (; j < nb; ++j) {
         const float* zb = ZB + ((int64_t)j * R + c) * N;
         float a = 0.0f;
 #pragma unroll
@@ -385,9 +406,20 @@ __global__ void reorth_update_kernel(const float* __restrict__ RB, int nb, int R
     __shared__ float sc[1024];
     for (int j = threadIdx.x; j < nb; j += blockDim.x) sc[j] = (float)coef[j * R + c];
     __syncthreads();
+    const int64_t stride = (int64_t)R * N;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         float v = r[(int64_t)c * N + i];
-        for (int j = 0; j < nb; ++j) v = fmaf(-sc[j], RB[((int64_t)j * R + c) * N + i], v);
+        const float* rb = RB + (int64_t)c * N + i;
+        int j = 0;
+        for (; j + 4 <= nb; j += 4) {   // four loads in flight; the same order of updates
+            const float b0 = rb[(int64_t)j * stride], b1 = rb[(int64_t)(j + 1) * stride];
+            const float b2 = rb[(int64_t)(j + 2) * stride], b3 = rb[(int64_t)(j + 3) * stride];
+            v = fmaf(-sc[j], b0, v);
+            v = fmaf(-sc[j + 1], b1, v);
+            v = fmaf(-sc[j + 2], b2, v);
+            v = fmaf(-sc[j + 3], b3, v);
+        }
+        for (; j < nb; ++j) v = fmaf(-sc[j], rb[(int64_t)j * stride], v);
         r[(int64_t)c * N + i] = v;
     }
 }
