@@ -192,7 +192,7 @@ GPK_API int gp_measure_peaks(gp_ctx* ctx, double* ex2_per_s, double* sqrt_per_s,
 GPK_API int gp_measure_peaks2(gp_ctx* ctx, double* ex2_per_s, double* sqrt_per_s, double* ffma_per_s,
                               double* pack_per_s, double* ex2pack_per_s, void* stream);
 
-/* ---- S1+S2: matrix-free kernel MVM (Eq. mvm, Sec. 4.1) --------------------
+/* ---- matrix-free kernel MVM (Eq. mvm, Sec. 4.1) ---------------------------
  *   out[:, c] = a^2 K(Xr, Xc) V[:, c]  (+ sigma^2 V[:, c] with GP_MVM_ADD_NOISE)
  * K is never stored: 128 x 128 tiles of the kernel matrix are formed on chip
  * (distance contraction on tensor cores, kernel function on the special
@@ -248,7 +248,7 @@ GPK_API int gp_kmvm_noalloc(const gp_hyp_t* hyp, const float* Xr, int64_t Nr, co
  * out), GP_ERR_NONFINITE, or GP_ERR_CUDA.  Allocates nothing. */
 GPK_API int gp_kmvm_noalloc_check(void* stream);
 
-/* ---- S3: pivoted-Cholesky preconditioner (Sec. 4.2, Eq. woodbury) ---------
+/* ---- pivoted-Cholesky preconditioner (Sec. 4.2, Eq. woodbury) -------------
  * k = rank steps of partial pivoted Cholesky of K (no noise) from kernel rows
  * K e_p and the constant diagonal a^2: pivot = argmax of the remaining
  * diagonal (lowest index on ties); stops early when that value falls to
@@ -274,7 +274,7 @@ typedef struct {
     int rank;
 } gp_precond_t;
 
-/* ---- S4-S6: preconditioned conjugate gradients (Alg. 1, Alg. 2, App. A) ---- */
+/* ---- preconditioned conjugate gradients (Alg. 1, Alg. 2, App. A) ---------- */
 #define GP_CG_STABLE     0  /* Alg. 2: log-scale alpha/beta (LSE), re-orthogonalisation */
 #define GP_CG_STANDARD   1  /* Alg. 1: textbook preconditioned CG                          */
 #define GP_REORTH_NONE   0
@@ -362,7 +362,7 @@ GPK_API int gp_cg_solve(gp_ctx* ctx, const gp_hyp_t* hyp, const float* X, int64_
                         float* U, const gp_precond_t* precond, const gp_cg_opts_t* opts, gp_cg_stats_t* stats,
                         void* stream);
 
-/* ---- NEXT #4: low-precision preconditioned MINRES (Conclusion, future work) --
+/* ---- low-precision preconditioned MINRES (Conclusion, future work) ----------
  * MINRES (Paige and Saunders' Lanczos-based minimum-residual method) for
  * (K + sigma^2 I) U = B with the same kernel MVM engines and the same
  * pivoted-Cholesky preconditioner P as gp_cg_solve: the Conclusion names the
@@ -417,7 +417,7 @@ GPK_API int gp_minres_solve(gp_ctx* ctx, const gp_hyp_t* hyp, const float* X, in
                             float* U, const gp_precond_t* precond, const gp_minres_opts_t* opts,
                             gp_minres_stats_t* stats, void* stream);
 
-/* ---- S7: backward of the kernel MVM (gradient of a bilinear form) ----------
+/* ---- backward of the kernel MVM (gradient of a bilinear form) --------------
  * grad_theta[0..d+2) = d/d(l_1..l_d, a^2, sigma^2) of  q = sum_c u_c^T Ktilde w_c,
  * and, when grad_X is not NULL, grad_X = dq/dX (device, N x d row-major).
  * With r^2 = sum_m (x_im - x_jm)^2 / l_m^2 and G_ij = sum_c u_ic w_jc:
@@ -448,7 +448,7 @@ GPK_API size_t gp_kmvm_vjp_prec_workspace_size(const gp_hyp_t* hyp, int64_t N, i
 GPK_API int gp_kmvm_vjp_prec(gp_ctx* ctx, const gp_hyp_t* hyp, const float* X, int64_t N, const float* U,
                              const float* W, int R, int precision, double* grad_theta, float* grad_X, void* stream);
 
-/* ---- S7: stochastic Lanczos quadrature from CG step sizes (host) -----------
+/* ---- stochastic Lanczos quadrature from CG step sizes (host) ---------------
  * out = gamma0 * e1^T log(T) e1 for the Lanczos tridiagonal T of a CG run
  * with step sizes alpha[0..J) and beta[0..J-1) (beta[k] = beta_{k+1} of
  * Alg. 2): T_kk = 1/alpha_k + beta_k/alpha_{k-1}, T_{k,k+1} = sqrt(beta_{k+1})/alpha_k.
@@ -456,7 +456,7 @@ GPK_API int gp_kmvm_vjp_prec(gp_ctx* ctx, const gp_hyp_t* hyp, const float* X, i
  * eigen-decomposition of T by implicit-shift QL. */
 GPK_API int gp_slq_quadrature(const double* alpha, const double* beta, int J, double gamma0, double* out);
 
-/* ---- S7: loss and gradient (Sec. 4.3, Eq. loss / approx_loss / approx) ------ */
+/* ---- loss and gradient (Sec. 4.3, Eq. loss / approx_loss / approx) ---------- */
 #define GP_MLL_PRECOND_PROBES 0x1  /* z_j = L e_j + sigma z~_j (E[zz^T] = P) from the
                                       standard normals Z (z~) and E; gradient pairs
                                       u_j with P^{-1} z_j; enables the SLQ log|Ktilde|
@@ -487,7 +487,7 @@ GPK_API int gp_mll_and_grad(gp_ctx* ctx, const gp_hyp_t* hyp, const float* X, co
                             const gp_cg_opts_t* opts, int flags, double* mll, double* grad, float* grad_X,
                             float* U, gp_cg_stats_t* stats, void* stream);
 
-/* ---- S8: serving with continuous batching (predictive mean, Sec. 2.1) ------- *
+/* ---- serving with continuous batching (predictive mean, Sec. 2.1) ----------- *
  * A server owns one device arena (allocated once by gp_server_create, never
  * grown) and a fixed number of request slots, each with its own CUDA stream.
  * An engine thread admits queued requests in arrival order whenever a slot is

@@ -1,4 +1,4 @@
-// S5 + S6: enhanced-stability preconditioned CG (Alg. 2) and textbook
+// Enhanced-stability preconditioned CG (Alg. 2) and textbook
 // preconditioned CG (Alg. 1), for R right-hand sides at once with per-column
 // scalars (mBCG, App. A).
 //

@@ -78,7 +78,7 @@ enum DevErr : int {
 constexpr uint64_t kWaitLimitNs = 1000000000ull;   // 1 s
 
 // ----------------------------------------------------------------------------
-// Operand preparation (S1): scaled inputs, norms, V scaling / casting.
+// Operand preparation: scaled inputs, norms, V scaling / casting.
 // ----------------------------------------------------------------------------
 struct OperandLayout {
     int prec = 0;    // GP_PREC_FP16 / GP_PREC_BF16
@@ -119,7 +119,7 @@ int launch_v_cast(Ctx* ctx, int prec, int scale_mode, int vsplit, const float* V
                   cudaStream_t s);
 
 // ----------------------------------------------------------------------------
-// MVM engines (S2)
+// MVM engines
 // ----------------------------------------------------------------------------
 struct MvmArgs {
     int kernel;

@@ -1,4 +1,4 @@
-// S2 (comparator arm): the same matrix-free MVM (Eq. mvm) in plain FP32 on the
+// The comparator arm: the same matrix-free MVM (Eq. mvm) in plain FP32 on the
 // CUDA cores -- the "single precision" side of the paper's half-vs-single
 // comparison (Sec. 4.1, Fig. 4a).  Squared distances are formed from
 // differences of the scaled inputs (no expanded-norm cancellation), the kernel

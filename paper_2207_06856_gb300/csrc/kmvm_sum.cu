@@ -1,4 +1,4 @@
-// NEXT #3: the summation-variant study of the half-precision MVM (Sec. 4.1,
+// The summation-variant study of the half-precision MVM (Sec. 4.1,
 // Fig. 4b; App. B, Fig. A.1a).  The paper's FP16 MVM runs on CUDA cores and
 // compares how the row sums sum_j k_ij v_j are accumulated.  This engine does
 // the same on this GPU: per pair the kernel value is rounded to FP16 and

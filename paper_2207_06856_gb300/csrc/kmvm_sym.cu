@@ -1,4 +1,4 @@
-// NEXT #4: the symmetric half-work kernel MVM (an extension in the direction of
+// The symmetric half-work kernel MVM (an extension in the direction of
 // the Conclusion's future work: K = K^T lets an MVM evaluate N (N + 1) / 2
 // kernel values instead of N^2).
 //

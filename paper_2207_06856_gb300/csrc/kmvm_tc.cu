@@ -1,4 +1,4 @@
-// S2: the tensor-core kernel MVM (Eq. mvm; Sec. 4.1).
+// The tensor-core kernel MVM (Eq. mvm; Sec. 4.1), one-row-tile engine.
 //
 //   out_i = a^2 sum_j k(x_i, x_j) v_j (+ sigma^2 v_i)
 //

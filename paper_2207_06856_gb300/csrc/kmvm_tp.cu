@@ -1,4 +1,4 @@
-// S2: the tensor-core kernel MVM with the transposed value product
+// The tensor-core kernel MVM with the transposed value product
 // (Eq. mvm; Sec. 4.1).
 //
 //   out_i = a^2 sum_j k(x_i, x_j) v_j (+ sigma^2 v_i)

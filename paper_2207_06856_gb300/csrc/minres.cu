@@ -1,4 +1,4 @@
-// NEXT #4 (second half): low-precision preconditioned MINRES (the Conclusion
+// Low-precision preconditioned MINRES (the Conclusion
 // names MINRES as a further iterative method for the paper's low- and
 // mixed-precision approach).
 //

@@ -1,4 +1,4 @@
-// S7: negative log marginal likelihood and its gradient (Sec. 4.3).
+// Negative log marginal likelihood and its gradient (Sec. 4.3).
 //
 // The solves K [u_0, u_1 .. u_M] = [y, z_1 .. z_M] of Eq. cg run through the
 // stable CG (Alg. 2).  With the solutions detached, the gradient of the

@@ -1,5 +1,5 @@
-// Kernel-MVM operator: prepares the input-side operands once (S1) and applies
-// K(Xr, Xc) V (+ sigma^2 V) any number of times (S2).  Used by gp_kmvm and by
+// Kernel-MVM operator: prepares the input-side operands once and applies
+// K(Xr, Xc) V (+ sigma^2 V) any number of times.  Used by gp_kmvm and by
 // every solver, so the MVM inside CG is exactly the MVM that gp_kmvm exposes.
 #include "gpk_internal.cuh"
 

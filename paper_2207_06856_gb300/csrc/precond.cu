@@ -1,4 +1,4 @@
-// S3 + S4: pivoted-Cholesky preconditioner and its Woodbury application
+// Pivoted-Cholesky preconditioner and its Woodbury application
 // (Sec. 4.2 "Preconditioning", Eq. woodbury).
 //
 // Factor.  k steps of partial pivoted Cholesky of K (no noise), using only

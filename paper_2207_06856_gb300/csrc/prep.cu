@@ -1,4 +1,4 @@
-// S1: operand preparation for the kernel MVM (Sec. 4.1 "Half Precision
+// Operand preparation for the kernel MVM (Sec. 4.1 "Half Precision
 // Matrix Vector Multiplies" and the downscaling paragraph that follows it).
 //
 // Tensor-core operands.  For point i with scaled inputs x^_i = c x_i / l (c

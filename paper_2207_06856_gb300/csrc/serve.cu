@@ -1,4 +1,4 @@
-// S8: serving GP posterior means with continuous batching.
+// Serving GP posterior means with continuous batching.
 //
 // A request is one solve Ktilde v = y (Alg. 2 with the pivoted-Cholesky
 // preconditioner of Eq. woodbury) followed by the predictive mean

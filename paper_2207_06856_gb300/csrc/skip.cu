@@ -1,4 +1,4 @@
-// NEXT #1 of the hot path: compact-support tile skipping (Sec. 3.1, "finite
+// Compact-support tile skipping for the tensor-core MVM (Sec. 3.1, "finite
 // precision kernels have finite support", Fig. 2c; App. C.1).
 //
 // In a finite format a stationary kernel is exactly zero beyond the distance at

@@ -1,4 +1,4 @@
-// S7 (part): backward of the kernel MVM -- the gradient of
+// Backward of the kernel MVM -- the gradient of
 //     q(theta, X) = sum_c u_c^T Ktilde(theta, X) w_c
 // with respect to theta = (l_1..l_d, a^2, sigma^2) and, optionally, X
 // (what Eq. approx needs: the pseudo-loss is such a bilinear form with the

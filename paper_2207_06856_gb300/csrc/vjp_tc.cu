@@ -1,4 +1,4 @@
-// S7: the backward of the kernel MVM on the tensor cores (Sec. 4.3, Eq. approx;
+// The backward of the kernel MVM on the tensor cores (Sec. 4.3, Eq. approx;
 // Sec. 2.2, Eq. gradient): the gradient of the bilinear form
 //     q = sum_c u_c^T Ktilde w_c
 // with respect to (l_1..l_d, a^2, sigma^2) and X, for RBF, Matern-3/2 and

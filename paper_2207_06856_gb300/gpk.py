@@ -643,7 +643,7 @@ def mll_and_grad(ctx: Context, hyp: Hyper, X, y, Z, precond: Precond | None = No
     return float(mll.value), g, gX, U, info
 
 
-# ---- S8: serving ------------------------------------------------------------------
+# ---- serving ----------------------------------------------------------------------
 
 
 def _server_opts(arena_bytes, max_slots, rank, precision, mean_precision, tol, max_iter, restarts, reorth,
