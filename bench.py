@@ -739,7 +739,8 @@ def serve_measure(args, n_requests, n_calib=None):
                      precision=sprec, mean_precision="fp32", tol=TOL,
                      max_iter=1000, restarts=4,
                      refine_precision="fp16" if args.serve_schedule == "relaxed" else None,
-                     refine_resid=RELAX_RESID if args.serve_schedule == "relaxed" else 0.0)
+                     refine_resid=RELAX_RESID if args.serve_schedule == "relaxed" else 0.0,
+                     large_n=args.serve_large_n, large_reserve=args.serve_large_reserve)
     small = workloads.serving(n_requests=3, rate_per_s=1.0, seed=2, n_min=1000, n_max=2000)
     for r in small:   # warm-up
         srv.submit(gpk.Hyper(r.kernel, r.lengthscale, r.outputscale, r.noise), r.X, r.y, r.Xstar).result()
@@ -794,7 +795,8 @@ def serve_measure(args, n_requests, n_calib=None):
                                   "split": "kernel tile and inputs as hi + lo",
                                   "fp32pv": "inputs as hi + lo, FP32 kernel values and value product"}[
                                    args.serve_schedule] + ") + stable CG to 1e-2, rank 20",
-                   "slots": args.serve_slots, "arena_gb": args.serve_arena_gb},
+                   "slots": args.serve_slots, "arena_gb": args.serve_arena_gb,
+                   "large_n": args.serve_large_n, "large_reserve_sms": args.serve_large_reserve},
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
         "mean_ms": float(lat.mean()), "solves_per_s": len(reqs) / wall, "saturated_solves_per_s": sat,
         "offered_rate_per_s": rate, "iters_p50": float(np.median(iters)), "iters_max": int(iters.max()),
@@ -972,6 +974,9 @@ def main():
                     help="serving CG MVM: FP32 kernel values and value product with hi + lo inputs (fp32pv, the "
                          "default), hi + lo tile and inputs throughout (split), or hi + lo until the residual is "
                          "30 x tol then single-rounded (relaxed; fails on low-noise requests)")
+    ap.add_argument("--serve-large-n", type=int, default=32768,
+                    help="serving: requests with N >= this leave --serve-large-reserve SMs to smaller ones")
+    ap.add_argument("--serve-large-reserve", type=int, default=16, help="serving: 0 = every request on all SMs")
     ap.add_argument("--arms", default="", help="comma-separated subset of the comparison arms (default: all)")
     ap.add_argument("--nrhs", type=int, default=0, help="kmvm mode: use the first NRHS right-hand sides (0: all 17)")
     ap.add_argument("--serve-requests", type=int, default=512)

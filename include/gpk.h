@@ -515,6 +515,14 @@ typedef struct {
                             recursive relative residual is <= refine_resid (> 0), or at
                             the first true-residual check (0): gp_cg_opts_t's fields */
     double refine_resid;
+    int64_t large_n;     /* requests with N >= large_n plan their kernels for all but
+                            large_reserve SMs, which stay free for the kernels of
+                            smaller requests (a large request's MVM otherwise holds
+                            every SM for milliseconds at a time); large_reserve = 0:
+                            every request uses all SMs.  A request's launch plans
+                            depend on its own N only, so its result is still the same
+                            alone and in a mix.                                      */
+    int large_reserve;
 } gp_server_opts_t;
 
 typedef struct {

@@ -158,6 +158,7 @@ int check_opts(const gp_server_opts_t* o) {
     if (!o || o->arena_bytes == 0 || o->max_slots < 1 || o->max_slots > 64) return GP_ERR_INVALID;
     if (o->rank < 0 || o->rank > 512 || !(o->tol >= 0.0) || o->max_iter < 1 || o->max_iter > 1000) return GP_ERR_INVALID;
     if (o->restarts < 0 || o->restarts > 16) return GP_ERR_INVALID;
+    if (o->large_reserve < 0 || o->large_n < 0) return GP_ERR_INVALID;
     if (o->reorth < GP_REORTH_NONE || o->reorth > GP_REORTH_EUCLID) return GP_ERR_INVALID;
     GPK_TRY(check_mvm_flags(o->precision, false));
     GPK_TRY(check_mvm_flags(o->mean_precision, false));
@@ -166,6 +167,12 @@ int check_opts(const gp_server_opts_t* o) {
         if (!(o->refine_resid >= 0.0) || (o->refine_resid == 0.0 && o->restarts < 1)) return GP_ERR_INVALID;
     }
     return GP_OK;
+}
+
+// SMs a request's kernels are planned for (its own N decides, not the mix).
+int request_sms(const gp_server_opts_t& o, int64_t N, int num_sms) {
+    if (o.large_reserve > 0 && N >= o.large_n && o.large_reserve < num_sms) return num_sms - o.large_reserve;
+    return num_sms;
 }
 
 // Footprint: persistent part + the largest phase scratch; 0 if not servable.
@@ -226,6 +233,7 @@ int Server::admit(Slot& sl, std::shared_ptr<Request> r, size_t off) {
     sl.req = r;
     sl.off = off;
     sl.phase = SOLVING;
+    sl.ctx.num_sms = request_sms(o, r->N, num_sms);
     const int64_t N = r->N;
     const int d = r->hyp.d;
     const int rank = o.rank < N ? o.rank : (int)N;
@@ -389,6 +397,7 @@ size_t gp_server_request_bytes(const gp_server_opts_t* opts, const gp_hyp_t* hyp
     int dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&probe.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) probe.num_sms = 148;
+    probe.num_sms = gpk::request_sms(*opts, N, probe.num_sms);
     return gpk::request_bytes(&probe, *opts, hyp, N, n_test, nullptr);
 }
 
@@ -494,7 +503,7 @@ int gp_server_submit(gp_server* srv, const gp_hyp_t* hyp, const float* X, int64_
     r->out_pinned = cudaPointerGetAttributes(&pa, mean_out) == cudaSuccess && pa.type == cudaMemoryTypeHost;
     cudaGetLastError();
     gpk::Ctx probe;
-    probe.num_sms = srv->num_sms;
+    probe.num_sms = gpk::request_sms(srv->o, N, srv->num_sms);
     r->bytes = gpk::request_bytes(&probe, srv->o, &r->hyp, N, n_test, nullptr);
     if (r->bytes == 0) return GP_ERR_INVALID;
     if (((r->bytes + 255) & ~size_t(255)) > srv->o.arena_bytes) return GP_ERR_WORKSPACE;

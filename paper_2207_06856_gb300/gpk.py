@@ -115,7 +115,8 @@ class _ServerOpts(ctypes.Structure):
     _fields_ = [("arena_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int), ("rank", ctypes.c_int),
                 ("precision", ctypes.c_int), ("mean_precision", ctypes.c_int), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("restarts", ctypes.c_int), ("reorth", ctypes.c_int),
-                ("refine_precision", ctypes.c_int), ("refine_resid", ctypes.c_double)]
+                ("refine_precision", ctypes.c_int), ("refine_resid", ctypes.c_double),
+                ("large_n", ctypes.c_int64), ("large_reserve", ctypes.c_int)]
 
 
 class _ReqStats(ctypes.Structure):
@@ -647,12 +648,12 @@ def mll_and_grad(ctx: Context, hyp: Hyper, X, y, Z, precond: Precond | None = No
 
 
 def _server_opts(arena_bytes, max_slots, rank, precision, mean_precision, tol, max_iter, restarts, reorth,
-                 refine_precision=None, refine_resid=0.0):
+                 refine_precision=None, refine_resid=0.0, large_n=0, large_reserve=0):
     return _ServerOpts(int(arena_bytes), int(max_slots), int(rank), PRECISIONS.get(precision, precision),
                        PRECISIONS.get(mean_precision, mean_precision), float(tol), int(max_iter), int(restarts),
                        REORTH.get(reorth, reorth),
                        0 if refine_precision is None else PRECISIONS.get(refine_precision, refine_precision),
-                       float(refine_resid))
+                       float(refine_resid), int(large_n), int(large_reserve))
 
 
 class ServeFuture:
@@ -692,14 +693,15 @@ class Server:
     (MVM_FP32_PV): over the serving workload's range of noise levels a single
     FP16 rounding of the kernel tile can leave the operator too inexact for CG
     to converge, and for one right-hand side the FP32 product is also twice as
-    fast as the hi + lo FP16 tile on the tensor cores."""
+    fast as the hi + lo FP16 tile on the tensor cores.  Requests with
+    N >= large_n leave large_reserve SMs to the kernels of smaller requests."""
 
     def __init__(self, device: int = 0, arena_bytes: int = 8 << 30, max_slots: int = 8, rank: int = 20,
                  precision=FP16 | MVM_XSPLIT | MVM_FP32_PV, mean_precision="fp32", tol: float = 1e-2,
                  max_iter: int = 1000, restarts: int = 4, reorth="pinv", refine_precision=None,
-                 refine_resid: float = 0.0):
+                 refine_resid: float = 0.0, large_n: int = 32768, large_reserve: int = 16):
         self.opts = _server_opts(arena_bytes, max_slots, rank, precision, mean_precision, tol, max_iter, restarts,
-                                 reorth, refine_precision, refine_resid)
+                                 reorth, refine_precision, refine_resid, large_n, large_reserve)
         h = _c_void_p()
         _check(lib().gp_server_create(int(device), ctypes.byref(self.opts), ctypes.byref(h)), "gp_server_create")
         self._h = h

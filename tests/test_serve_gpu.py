@@ -102,11 +102,14 @@ def test_serve_fp16_within_cg_bound(gpk, relaxed):
 
 
 @pytest.mark.gpu
-def test_same_result_alone_and_in_mix(gpk):
+@pytest.mark.parametrize("large_n", [32768, 1500])
+def test_same_result_alone_and_in_mix(gpk, large_n):
     """Each request served alone (one at a time) and in a mix of twelve with
-    up to six in flight gives bit-identical means; the mix really overlapped."""
+    up to six in flight gives bit-identical means; the mix really overlapped.
+    With large_n = 1500 the larger half of the requests plan their kernels for
+    all but 16 SMs: still the same result alone and in the mix."""
     reqs = _requests(12, seed=7)
-    srv = gpk.Server(0, arena_bytes=2 << 30, max_slots=6, rank=20)
+    srv = gpk.Server(0, arena_bytes=2 << 30, max_slots=6, rank=20, large_n=large_n, large_reserve=16)
     try:
         alone = []
         for r in reqs:
