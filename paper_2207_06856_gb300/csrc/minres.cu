@@ -1,13 +1,12 @@
-// Low-precision preconditioned MINRES (the Conclusion
-// names MINRES as a further iterative method for the paper's low- and
-// mixed-precision approach).
+// Low-precision preconditioned MINRES (the Conclusion names MINRES as a
+// further iterative method for the paper's low- and mixed-precision approach).
 //
 // MINRES for Ktilde U = B, Ktilde = K + sigma^2 I, preconditioned by the SPD
 // pivoted-Cholesky/Woodbury operator P (Eq. woodbury), all R columns at once:
 // each column runs the Lanczos process of P^-1 Ktilde in the P inner product
 // in the form of Paige and Saunders' MINRES (r1, r2: the last two unnormalised
 // Lanczos vectors, y = P^-1 r2, v = y / beta with beta = sqrt(r2^T y), the
-// next vector from Ktilde v - alpha r2 - (beta / beta_old) r1),
+// next vector from Ktilde v - (alpha / beta) r2 - (beta / beta_old) r1),
 // and updates the QR factorisation of its tridiagonal matrix with one Givens
 // rotation per step; the search direction w and the iterate x follow from
 // the rotation, and phibar is the residual's P^-1 norm (the quantity MINRES
