@@ -597,11 +597,13 @@ def run_minres(args):
         return float(rel2.max()), float(relp.max())
 
     out = {}
-    for name, prec in (("minres_fp16_single", "fp16"), ("minres_fp16_hi_lo", split), ("minres_fp32", "fp32")):
-        def solve_m(prec=prec):
+    for name, prec, ref in (("minres_fp16_single", "fp16", None), ("minres_fp16_hi_lo", split, None),
+                            ("minres_relaxed", split, "fp16"), ("minres_fp32", "fp32", None)):
+        def solve_m(prec=prec, ref=ref):
             pc = gpk.pivchol(ctx, hyp, X, w.rank)
             return gpk.minres_solve(ctx, hyp, X, B, pc, tol=TOL * (1.0 - args.stop_margin), max_iter=MAX_ITER,
-                                    precision=prec, restarts=8, norm="2")
+                                    precision=prec, restarts=8, norm="2", refine_precision=ref,
+                                    refine_resid=RELAX_RESID if ref else 0.0)
         t, (U, st, info) = timed(solve_m)
         r2, rp = verify(U)
         out[name] = {"s_per_solve": t, "status": int(st), "iters": int(info["iters"]),

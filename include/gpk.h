@@ -388,6 +388,11 @@ typedef struct {
                             check each column's recurrence stops at
                             tol * 0.95 * (P^-1-norm / 2-norm of its recomputed
                             residual), the norms' observed ratio.  Needs restarts > 0. */
+    int refine_precision; /* 0 = off; else MVM flags the solve switches to once the
+                            recurrence's relative residual of every active column is
+                            <= refine_resid (> 0), with the stagnation guard of
+                            gp_cg_opts_t: the relaxed schedule of the CG solve     */
+    double refine_resid;
 } gp_minres_opts_t;
 #define GP_MINRES_NORM_P 0
 #define GP_MINRES_NORM_2 1

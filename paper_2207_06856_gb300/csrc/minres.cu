@@ -315,16 +315,21 @@ mr_scalar_kernel(int mode, const double* __restrict__ part, int nblk, int R, MrS
         if (__shfl_sync(0xffffffffu, last, 0)) {
             __threadfence();
             int cnt = 0, brk = 0;
+            float rmax = 0.0f;   // largest relative residual of the active columns
             for (int q = l; q < R; q += 32) {
-                cnt += *(volatile const int*)&st[q].active != 0;
+                const bool a = *(volatile const int*)&st[q].active != 0;
+                cnt += a;
                 brk += *(volatile const int*)&st[q].breakdown != 0;
+                if (a) rmax = fmaxf(rmax, (float)*(volatile const double*)&st[q].relres);
             }
             cnt = __reduce_add_sync(0xffffffffu, cnt);
             brk = __reduce_add_sync(0xffffffffu, brk);
+            const unsigned rbits = __reduce_max_sync(0xffffffffu, __float_as_uint(rmax));
             if (l == 0) {
                 nact[0] = cnt;
                 nact[1] = brk;
                 nact[2] = 0;
+                nact[3] = (int)rbits;
             }
         }
     }
@@ -350,6 +355,10 @@ int check_minres_args(const gp_hyp_t* hyp, int64_t N, int R, const gp_minres_opt
     if (o->restarts < 0 || o->restarts > 16) return GP_ERR_INVALID;
     if (o->norm != GP_MINRES_NORM_P && o->norm != GP_MINRES_NORM_2) return GP_ERR_INVALID;
     if (o->norm == GP_MINRES_NORM_2 && o->restarts < 1) return GP_ERR_INVALID;
+    if (o->refine_precision != 0) {
+        GPK_TRY(check_mvm_flags(o->refine_precision, false));
+        if (!(o->refine_resid > 0.0)) return GP_ERR_INVALID;
+    }
     GPK_TRY(check_mvm_flags(o->precision, false));
     GPK_TRY(check_mvm_flags(o->check_precision, false));
     return GP_OK;
@@ -360,6 +369,8 @@ size_t minres_workspace(const Ctx* ctx, const gp_hyp_t* hyp, int64_t N, int R, i
     mr_layout(c, N, R, rank, o);
     size_t s = c.off + kop_workspace(ctx, hyp, N, N, R, o->precision, true);
     if (o->check_precision != o->precision) s += kop_workspace(ctx, hyp, N, N, R, o->check_precision, true);
+    if (o->refine_precision != 0 && o->refine_precision != o->precision && o->refine_precision != o->check_precision)
+        s += kop_workspace(ctx, hyp, N, N, R, o->refine_precision, true);
     if (rank > 0) s += woodbury_workspace(ctx, N, rank, R);
     return s;
 }
@@ -383,8 +394,12 @@ struct MrSolve {
     int* nact;
     double* rhist;
     double* cinv = nullptr;
-    KOp op, op_chk_own;
+    KOp op, op_chk_own, op_ref_own;
     KOp* op_chk = nullptr;
+    KOp* op_ref = nullptr;     // the relaxed schedule's MVM
+    bool refined = false, relax_off = false;
+    int k_sw = 0;
+    float r_sw = 0.0f;
     WsCarver wc_rest{nullptr, 0};
 
     int launched(int n) {
@@ -417,7 +432,7 @@ struct MrSolve {
         return woodbury_apply(ctx, wtmp, pc.L, pc.core, cinv, rank, hyp.noise, N, W, R, mask, Z, s);
     }
     int flag_copy_wait() {
-        GPK_CUDA_TRY(cudaMemcpyAsync(ctx->host_pinned, nact, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        GPK_CUDA_TRY(cudaMemcpyAsync(ctx->host_pinned, nact, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
         GPK_CUDA_TRY(cudaStreamSynchronize(s));
         return GP_OK;
     }
@@ -439,12 +454,34 @@ struct MrSolve {
         GPK_CUDA_TRY(cudaMemsetAsync(w2, 0, sizeof(float) * NR, s));
         return flag_copy_wait();
     }
+    // the relaxed schedule of gp_cg_opts_t: switch once every active residual is at
+    // most refine_resid; after a switch below the start, return to the solve's MVM
+    // if the largest residual has not halved within max(20, k_sw / 4) iterations or
+    // has doubled
+    void relax_step(int k) {
+        if (o.refine_precision == 0 || !(o.refine_resid > 0.0) || relax_off || ctx->host_pinned[0] == 0) return;
+        float rmax;
+        memcpy(&rmax, &ctx->host_pinned[3], sizeof(rmax));
+        if (!refined) {
+            if ((double)rmax <= o.refine_resid) {
+                refined = true;
+                k_sw = k;
+                r_sw = rmax;
+            }
+        } else {
+            const int W = k_sw / 4 > 20 ? k_sw / 4 : 20;
+            if (r_sw < 1.0f && (rmax > 2.0f * r_sw || (k - k_sw >= W && rmax > 0.5f * r_sw))) {
+                refined = false;
+                relax_off = true;
+            }
+        }
+    }
     int iterate(int k) {
         const dim3 gcol((unsigned)vg, (unsigned)R);
         const dim3 gdot((unsigned)nblk, (unsigned)R);
         mr_scale_kernel<<<gcol, 256, 0, s>>>(v, y, N, st);
         GPK_TRY(launched(1));
-        GPK_TRY(kop_apply(ctx, op, v, R, av, N, true, s));
+        GPK_TRY(kop_apply(ctx, refined ? *op_ref : op, v, R, av, N, true, s));
         mr_lanczos1_kernel<<<gdot, kMrThreads, 0, s>>>(y, av, r1, v, N, nblk, st, part);
         GPK_TRY(launched(1));
         GPK_TRY(scalar(MR_ALPHA, k, 0));
@@ -506,6 +543,15 @@ int minres_run(Ctx* ctx, WsCarver& wc, const gp_hyp_t* hyp, const float* X, int6
         GPK_TRY(kop_prepare(ctx, wc, S.op_chk_own, hyp, X, N, X, N, R, o->check_precision, s));
         S.op_chk = &S.op_chk_own;
     }
+    S.op_ref = &S.op;
+    if (o->refine_precision != 0 && o->refine_precision != o->precision) {
+        if (o->refine_precision == o->check_precision) {
+            S.op_ref = S.op_chk;
+        } else {
+            GPK_TRY(kop_prepare(ctx, wc, S.op_ref_own, hyp, X, N, X, N, R, o->refine_precision, s));
+            S.op_ref = &S.op_ref_own;
+        }
+    }
     S.wc_rest = wc;
     S.vg = mr_grid(ctx, N);
     GPK_TRY(S.dots(B, B, true));
@@ -515,6 +561,7 @@ int minres_run(Ctx* ctx, WsCarver& wc, const gp_hyp_t* hyp, const float* X, int6
     bool checked = false;   // the state holds recomputed residuals of the final iterate
     for (;;) {
         if (ctx->host_pinned[0] > 0 && k < o->max_iter) {
+            S.relax_step(k);
             GPK_TRY(S.iterate(k));
             ++k;
             checked = false;

@@ -95,7 +95,8 @@ class _CgStats(ctypes.Structure):
 
 class _MinresOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
-                ("restarts", ctypes.c_int), ("check_precision", ctypes.c_int), ("norm", ctypes.c_int)]
+                ("restarts", ctypes.c_int), ("check_precision", ctypes.c_int), ("norm", ctypes.c_int),
+                ("refine_precision", ctypes.c_int), ("refine_resid", ctypes.c_double)]
 
 
 class _MinresStats(ctypes.Structure):
@@ -448,11 +449,12 @@ def cg_solve(ctx: Context, hyp: Hyper, X, B, precond: Precond | None = None, tol
 
 def minres_solve(ctx: Context, hyp: Hyper, X, B, precond: Precond | None = None, tol: float = 1e-2,
                  max_iter: int = 200, precision="fp16", flags: int = 0, restarts: int = 4, check_precision="fp32",
-                 norm: str = "p", stream=None):
+                 norm: str = "p", refine_precision=None, refine_resid: float = 0.0, stream=None):
     """gp_minres_solve: (K + sigma^2 I) U = B by preconditioned MINRES.
     B (R, N) -> (U (R, N), status, info).  tol applies to the residual in the
     P^-1 norm (norm="p") or, at the true-residual checks, in the 2-norm
-    (norm="2"); info holds per-column iterations, the final 2-norm and P^-1-norm
+    (norm="2"); refine_precision / refine_resid: the relaxed MVM schedule of
+    cg_solve; info holds per-column iterations, the final 2-norm and P^-1-norm
     relative residuals (recomputed with the check MVM) and the recurrence's
     P^-1-norm residual history.  status is GP_OK, GP_ERR_NOT_CONVERGED or
     GP_ERR_BREAKDOWN (other errors raise)."""
@@ -461,7 +463,8 @@ def minres_solve(ctx: Context, hyp: Hyper, X, B, precond: Precond | None = None,
     R = B.shape[0]
     prec = (PRECISIONS[precision] if isinstance(precision, str) else int(precision)) | int(flags)
     opts = _MinresOpts(float(tol), int(max_iter), prec, int(restarts), _check_flags(check_precision, prec),
-                       {"p": 0, "2": 1}[norm])
+                       {"p": 0, "2": 1}[norm],
+                       0 if refine_precision is None else _check_flags(refine_precision, prec), float(refine_resid))
     h = hyp.c()
     rank = precond.rank if precond is not None else 0
     need = int(lib().gp_minres_workspace_size(ctypes.byref(h), N, R, rank, ctypes.byref(opts)))

@@ -86,7 +86,7 @@ def test_minres_fp32_follows_the_oracle(ctx, kern):
     np.testing.assert_allclose(info["rel_resid"], rel2, rtol=0.05, atol=1e-6)
 
 
-@pytest.mark.parametrize("prec", ["fp16", "split", "bf16"])
+@pytest.mark.parametrize("prec", ["fp16", "split", "bf16", "relaxed"])
 def test_minres_low_precision_on_the_precision_workload(ctx, prec):
     """N = 6,000 drawn like the precision workload, 1 + 16 right-hand sides,
     rank-100 preconditioner, tolerance 1e-2 on the 2-norm residual at the FP32
@@ -99,10 +99,12 @@ def test_minres_low_precision_on_the_precision_workload(ctx, prec):
     Xd = _dev(w.X)
     B = w.rhs()
     pc = gpk.pivchol(ctx, hyp, Xd, w.rank)
-    p = gpk.FP16 | gpk.MVM_PSPLIT | gpk.MVM_XSPLIT if prec == "split" else prec
+    split = gpk.FP16 | gpk.MVM_PSPLIT | gpk.MVM_XSPLIT
+    p = split if prec in ("split", "relaxed") else prec
     tol = w.tol * 0.99   # 1 % under 1e-2 for the FP32 check's rounding, as for CG
+    relax = dict(refine_precision="fp16", refine_resid=0.3) if prec == "relaxed" else {}
     U, st, info = gpk.minres_solve(ctx, hyp, Xd, _dev(B), pc, tol=tol, max_iter=400, precision=p, restarts=4,
-                                   norm="2")
+                                   norm="2", **relax)
     ctx.check()
     assert st == gpk.GP_OK, (info["rel_resid"], info["iters"])
     oh = O.Hyp(workloads.KERNEL_NAMES[w.kernel], w.lengthscale, w.outputscale, w.noise)
